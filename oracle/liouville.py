@@ -1,0 +1,211 @@
+"""Level-set advection through the phase-space Liouville equation (oracle, float64).
+
+Test infrastructure only.
+
+Eq. 16 states that every level-set function phi is constant along the bicharacteristics; Eq. 19
+applies it to the position label X, the angle label vartheta and, with the source p_3 + p_1 dx/dz,
+to the traveltime tau; Eq. 20 initialises the labels to the phase-space coordinates and tau to 0.
+
+The paper marches in depth z, which limits it to rays with dz/dtau > 0 (Eq. 13).  Here the same
+equations are taken in pseudo-time t on the full reduced phase space (x, z, theta), theta in [0, 2pi):
+    d_t u + Vx d_x u + Vz d_z u + thetadot d_theta u = s_u,   s = 0 for labels, s = 1 for tau
+(with H normalised so that t is traveltime, the tau source p.V equals 1; Eq. 19's source is this one
+divided by dz/dt).  Labels: Yx, Yz (the position label of Eq. 20, two components, stored relative to
+the source x_s), Th (the angle label vartheta), tau.  The initial surface of Eq. 20 (the plane
+z = z_s) is replaced by a small ball B = {|x - x_s| <= r0} around the point source whose cells are
+frozen at the initial data
+    Y = x - x_s,  Th = theta,  tau = p_s(theta) . (x - x_s)
+(p_s the slowness of the medium at the source; exact in a locally homogeneous ball because p.V = 1).
+Two ghost layers in x and z hold the same initial data permanently (Dirichlet inflow); theta is
+periodic.  Angle-label differences are wrapped into [-pi, pi).
+
+Discretisation: Jiang & Peng's third-order HJ-WENO in each of x, z, theta, upwinded by the sign of
+the velocity component; Shu & Osher's TVD-RK3; dt = cfl / max_cells(|Vx|/hx + |Vz|/hz +
+|thetadot|/dtheta).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import christoffel as _ch
+from . import medium as _md
+
+FIELDS = ('Yx', 'Yz', 'Th', 'tau')
+WENO_EPS_REL = 1e-6
+GHOST = 2
+
+
+def _wrap(d):
+    return (d + np.pi) % (2.0 * np.pi) - np.pi
+
+
+class Setup:
+    """Everything the evolution needs for one 2-D problem (float64)."""
+
+    def __init__(self, problem):
+        self.p = problem
+        nx, nz, nth = problem.nx, problem.nz, problem.n_theta
+        self.nx, self.nz, self.nth = nx, nz, nth
+        self.hx, self.hz = float(problem.hx), float(problem.hz)
+        self.dth = 2.0 * math.pi / nth
+        self.a, self.da_dx, self.da_dz, self.rho = _md.medium_2d(problem)
+        self.vel = _ch.velocity_field_2d(self.a, self.da_dx, self.da_dz, nth)
+        self.xs = np.array(problem.xs, np.float64)
+        self.a_s = _md.bilinear_at(self.a, problem, self.xs[0], self.xs[1])
+        self.rho_s = float(_md.bilinear_at(self.rho, problem, self.xs[0], self.xs[1]))
+        self.theta = self.dth * np.arange(nth)
+        vs, _, _, _ = _ch.source_quantities(self.a_s, self.theta)
+        self.ps = np.stack([np.sin(self.theta) / vs, np.cos(self.theta) / vs], axis=-1)
+        self.c_ref = float(_ch.source_quantities(self.a_s, np.array([0.0]))[0][0])
+        self.r0 = float(problem.ball_radius)
+        # node coordinates including the ghost layers
+        ox, oz = problem.origin
+        self.xg = ox + self.hx * np.arange(-GHOST, nx + GHOST)
+        self.zg = oz + self.hz * np.arange(-GHOST, nz + GHOST)
+        dx = self.xg[GHOST:-GHOST] - self.xs[0]
+        dz = self.zg[GHOST:-GHOST] - self.xs[1]
+        self.ball = (dz[:, None] * dz[:, None] + dx[None, :] * dx[None, :]) <= self.r0 * self.r0
+        rate = (np.abs(self.vel['Vx']) / self.hx + np.abs(self.vel['Vz']) / self.hz
+                + np.abs(self.vel['thetadot']) / self.dth)
+        self.max_rate = float(rate.max())
+        h = max(self.hx, self.hz)
+        self.eps = {'Yx': WENO_EPS_REL * h * h, 'Yz': WENO_EPS_REL * h * h,
+                    'Th': WENO_EPS_REL * self.dth ** 2,
+                    'tau': WENO_EPS_REL * (h / self.c_ref) ** 2}
+
+    def dt(self, cfl):
+        return cfl / self.max_rate
+
+    def initial_state(self):
+        """Eq. 20 on the padded grid: Y = x - x_s, Th = theta, tau = p_s(theta) . (x - x_s)."""
+        X = (self.xg - self.xs[0])[None, None, :]
+        Z = (self.zg - self.xs[1])[None, :, None]
+        shape = (self.nth, self.nz + 2 * GHOST, self.nx + 2 * GHOST)
+        st = {
+            'Yx': np.broadcast_to(X, shape).copy(),
+            'Yz': np.broadcast_to(Z, shape).copy(),
+            'Th': np.broadcast_to(self.theta[:, None, None], shape).copy(),
+            'tau': self.ps[:, 0][:, None, None] * X + self.ps[:, 1][:, None, None] * Z,
+        }
+        return st
+
+
+def _weno3_pair(dm2, dm1, d0, dp1, eps):
+    """Jiang-Peng third-order HJ-WENO one-sided derivatives from undivided first differences.
+
+    d_j = u_{j+1} - u_j around cell i: dm2 = d_{i-2}, dm1 = d_{i-1}, d0 = d_i, dp1 = d_{i+1}.
+    Left-biased:  u^- = (d_{i-1} + d_i)/2 - w^-/2 (d_{i-2} - 2 d_{i-1} + d_i),
+                  w^- = 1/(1 + 2 r^2), r = (eps + (d_{i-1} - d_{i-2})^2) / (eps + (d_i - d_{i-1})^2)
+    Right-biased: u^+ = (d_{i-1} + d_i)/2 - w^+/2 (d_{i+1} - 2 d_i + d_{i-1}),
+                  w^+ = 1/(1 + 2 r^2), r = (eps + (d_{i+1} - d_i)^2) / (eps + (d_i - d_{i-1})^2)
+    (both undivided; divide by the spacing).
+    """
+    centre = 0.5 * (dm1 + d0)
+    rm = (eps + (dm1 - dm2) ** 2) / (eps + (d0 - dm1) ** 2)
+    wm = 1.0 / (1.0 + 2.0 * rm * rm)
+    um = centre - 0.5 * wm * (dm2 - 2.0 * dm1 + d0)
+    rp = (eps + (dp1 - d0) ** 2) / (eps + (d0 - dm1) ** 2)
+    wp = 1.0 / (1.0 + 2.0 * rp * rp)
+    up = centre - 0.5 * wp * (dp1 - 2.0 * d0 + dm1)
+    return um, up
+
+
+def upwind_derivatives(u, S, eps, angle):
+    """Upwind WENO3 derivatives (d_x u, d_z u, d_theta u) on the interior cells of padded u."""
+    nz, nx, G = S.nz, S.nx, GHOST
+    core = u[:, G:G + nz, G:G + nx]
+    shifts = {
+        'x': {k: u[:, G:G + nz, G + k:G + k + nx] for k in range(-2, 3)},
+        'z': {k: u[:, G + k:G + k + nz, G:G + nx] for k in range(-2, 3)},
+        'theta': {k: np.roll(core, -k, axis=0) for k in range(-2, 3)},
+    }
+    out = []
+    for name, h, vel in (('x', S.hx, S.vel['Vx']), ('z', S.hz, S.vel['Vz']),
+                         ('theta', S.dth, S.vel['thetadot'])):
+        s = shifts[name]
+        d = {j: s[j + 1] - s[j] for j in (-2, -1, 0, 1)}
+        if angle:
+            d = {j: _wrap(v) for j, v in d.items()}
+        um, up = _weno3_pair(d[-2], d[-1], d[0], d[1], eps)
+        out.append(np.where(vel > 0, um, up) / h)
+    return out
+
+
+def rhs(state, S):
+    """L(u) = -(Vx u_x + Vz u_z + thetadot u_theta) + s_u on interior cells; 0 in the frozen ball."""
+    out = {}
+    for f in FIELDS:
+        ux, uz, ut = upwind_derivatives(state[f], S, S.eps[f], angle=(f == 'Th'))
+        L = -(S.vel['Vx'] * ux + S.vel['Vz'] * uz + S.vel['thetadot'] * ut)
+        if f == 'tau':
+            L = L + 1.0
+        L[:, S.ball] = 0.0
+        out[f] = L
+    return out
+
+
+def _interior(u, S):
+    return u[:, GHOST:GHOST + S.nz, GHOST:GHOST + S.nx]
+
+
+def rk3_step(state, S, dt):
+    """Shu-Osher TVD-RK3: u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+    u_new = 1/3 u + 2/3 (u2 + dt L(u2)).  Ghost layers and frozen ball cells keep their initial
+    data bit for bit (they are copied, not recombined)."""
+    def combine(a, u, b, v, L):
+        w = {f: state[f].copy() for f in FIELDS}
+        for f in FIELDS:
+            _interior(w[f], S)[...] = a * _interior(u[f], S) + b * (_interior(v[f], S) + dt * L[f])
+            _interior(w[f], S)[:, S.ball] = _interior(state[f], S)[:, S.ball]
+        return w
+    L0 = rhs(state, S)
+    u1 = combine(0.0, state, 1.0, state, L0)
+    L1 = rhs(u1, S)
+    u2 = combine(0.75, state, 0.25, u1, L1)
+    L2 = rhs(u2, S)
+    return combine(1.0 / 3.0, state, 2.0 / 3.0, u2, L2)
+
+
+def _evolve_c(S, state, dt, steps):
+    """The same TVD-RK3 / WENO3 steps run by the compiled float64 loop in liouville_c.c."""
+    import ctypes
+    from .build import library
+    lib = library()
+    vel = [np.ascontiguousarray(S.vel[k], np.float64) for k in ('Vx', 'Vz', 'thetadot')]
+    ball = np.ascontiguousarray(S.ball, np.uint8)
+    eps = np.array([S.eps[f] for f in FIELDS], np.float64)
+    fields = [np.ascontiguousarray(state[f], np.float64).copy() for f in FIELDS]
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.oracle_rk3_steps(S.nth, S.nz, S.nx, S.hx, S.hz, S.dth, ptr(vel[0]), ptr(vel[1]),
+                              ptr(vel[2]), ptr(ball), ptr(eps), dt, int(steps),
+                              *[ptr(f) for f in fields])
+    if rc != 0:
+        raise MemoryError('oracle stepping could not allocate its stage buffers')
+    return dict(zip(FIELDS, fields))
+
+
+def evolve(problem, steps=None, cfl=None, S=None, state=None, backend='c'):
+    """Advance the labels `steps` TVD-RK3 steps from Eq. 20's initial data.  Returns (S, state, dt).
+
+    backend 'c' runs the compiled loop (liouville_c.c), 'numpy' the array code above; both compute
+    the same float64 scheme.
+    """
+    if S is None:
+        S = Setup(problem)
+    steps = problem.steps if steps is None else steps
+    cfl = problem.cfl if cfl is None else cfl
+    dt = S.dt(cfl)
+    if state is None:
+        state = S.initial_state()
+    if backend == 'c':
+        return S, _evolve_c(S, state, dt, steps), dt
+    for _ in range(steps):
+        state = rk3_step(state, S, dt)
+    return S, state, dt
+
+
+def interior_state(state, S):
+    """Interior (unpadded) copies of the four fields, shape (n_theta, nz, nx)."""
+    return {f: _interior(state[f], S).copy() for f in FIELDS}

@@ -1,0 +1,262 @@
+"""Gaussian-beam superposition and arrival extraction (oracle, float64).  Test infrastructure only.
+
+The paper forms a Gaussian beam about each point of the source manifold Gamma = {X = x_s} (Eq. 35)
+with complex traveltime tau + p.(x - X) + 1/2 (x - X)^T M (x - X) (Eq. 25, M = B C^-1 from the
+dynamic ray tracing of Eq. 21 with the complex initial data of Eq. 24), amplitude from det C
+(Eq. 26), and sums the beams over Gamma with the weight Psi_0 of Eq. 33 (Eq. 34).
+
+Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only):
+
+* Beams are centred at every receiver phase cell (x0, theta) and evaluated at the source; by the
+  reciprocity of the elastic Green's function this sums the same beams, and every beam centre is a
+  grid cell (the paper's advantage (2): no interpolation).  The ray through (x0, theta) carries the
+  level-set labels (Y, vartheta, tau); its impact parameter at the source is
+      b = (Y - x_s) x g_s(vartheta)          (2-D cross product a x b = a_x b_z - a_z b_x)
+  with g_s the unit group direction of the source medium, so Gamma = {b = 0} (Eq. 35).
+* Dynamic ray tracing from the level sets: a phase-space perturbation (dx, dz, dtheta) at the cell
+  moves the source-end invariants by (db, dvartheta) = grad(b, vartheta) . (dx, dz, dtheta), with
+  the gradients taken by centred differences of the labels.  The beam launched from x0 has the
+  complex initial perturbation dx = n_theta (unit wavefront tangent), dtheta = kappa with
+  kappa = -2 i v(x0, theta) / (omega w0^2), so its wavefront Hessian has imaginary part 2/(omega w0^2)
+  (|beam| falls to 1/e at w0: the beam-width parameter of Eq. 24).
+* At the source (a homogeneous ball) the reversed beam's transverse Hessian is
+      m = -(|V_s| / v_s^2) dvartheta / db
+  and its phase there is exactly tau(x0, theta) + m b^2 / 2 (the linear term of Eq. 25 vanishes
+  because tau carries the plane-wave time p_s . (Y - x_s) at the ball).
+* Amplitude (Eq. 26 with the elastic transport div(rho U^2 V) = 0):
+      sqrt(rho_r v_r / (rho_s |V_s| db)) on the principal branch, times -1 where d_theta b > 0 (one
+      caustic passed: the middle branch of a triplication; KMAH index 1).
+* Weight (the calibrated Psi_0 of Eqs. 30-33): i c_ref^2 / (4 pi v_r^2 rho_r) dtheta, output scaled
+  by rho_s c_ref^2 with c_ref the source phase velocity along +z, so that a homogeneous isotropic
+  medium gives the 2-D Helmholtz Green's function (i/4) H0^(1)(kr) as kr -> inf.  Phase convention
+  exp(+i omega T) from Eq. 2.
+* Only rays that left the source ball count: a cell is taken with weight taper(|Y - x_s|) = 1 below
+  r0 + h, 0 above r0 + 3h, raised cosine between.
+
+Arrivals (late arrivals included, Eq. 35): along theta at a node, every sign change of b between
+cells k and k+1 (sign(0) = +1) where both cells have |Y - x_s| <= r0 + 2h; T is tau interpolated
+linearly at b = 0 and A the geometrical amplitude |u| sqrt(omega) of that ray,
+      A = c_ref^2 sqrt(rho_s / rho_r) / (v_r sqrt(8 pi |V_s| |d_theta b|)),
+interpolated the same way.  Arrivals are sorted by T (then by angle index), at most kmax kept.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import christoffel as _ch
+
+
+def _wrap(d):
+    return (d + np.pi) % (2.0 * np.pi) - np.pi
+
+
+def _grad_axis(f, h, axis, wrap):
+    """Second-order centred difference along x or z, second-order one-sided at the two edges."""
+    f = np.moveaxis(f, axis, -1)
+    out = np.empty_like(f)
+    d = (lambda a: _wrap(a)) if wrap else (lambda a: a)
+    out[..., 1:-1] = d(f[..., 2:] - f[..., :-2]) / (2 * h)
+    out[..., 0] = (4 * d(f[..., 1] - f[..., 0]) - d(f[..., 2] - f[..., 0])) / (2 * h)
+    out[..., -1] = (4 * d(f[..., -1] - f[..., -2]) - d(f[..., -1] - f[..., -3])) / (2 * h)
+    return np.moveaxis(out, -1, axis)
+
+
+def _grad_theta(f, dth, wrap):
+    d = np.roll(f, -1, axis=0) - np.roll(f, 1, axis=0)
+    if wrap:
+        d = _wrap(d)
+    return d / (2 * dth)
+
+
+def taper(dist, r0, h):
+    """1 for dist <= r0 + h, 0 for dist >= r0 + 3h, raised cosine in between."""
+    t = np.clip((dist - (r0 + h)) / (2 * h), 0.0, 1.0)
+    return 0.5 * (1.0 + np.cos(np.pi * t))
+
+
+def beam_fields(S, lab):
+    """Frequency-independent per-cell quantities of the superposition (all float64)."""
+    Yx, Yz, Th, tau = lab['Yx'], lab['Yz'], lab['Th'], lab['tau']
+    vs, _, Vsn, ghat = _ch.source_quantities(S.a_s, Th)
+    b = Yx * ghat[..., 1] - Yz * ghat[..., 0]
+    h = max(S.hx, S.hz)
+    dist = np.sqrt(Yx * Yx + Yz * Yz)
+    return dict(
+        b=b, tau=tau, vs=vs, Vsn=Vsn, dist=dist, Th=Th,
+        bx=_grad_axis(b, S.hx, 2, False), bz=_grad_axis(b, S.hz, 1, False),
+        bt=_grad_theta(b, S.dth, False),
+        Tx=_grad_axis(Th, S.hx, 2, True), Tz=_grad_axis(Th, S.hz, 1, True),
+        Tt=_grad_theta(Th, S.dth, True),
+        w=taper(dist, S.r0, h), flag=dist <= S.r0 + 2 * h,
+    )
+
+
+def _interp(a, i0, i1, t):
+    return a[i0] + t * (a[i1] - a[i0])
+
+
+def crossings(S, lab, F, axis):
+    """Points of the source manifold Gamma = {b = 0} on grid rows (axis=2) or columns (axis=1).
+
+    For each theta and each row (column), every sign change of b between neighbouring nodes
+    (both flagged as ball-origin, sign(0) = +1) is one beam centre; its position and every per-cell
+    quantity are interpolated linearly between the two nodes.  Returns a dict of 1-D arrays.
+    """
+    b, flag = F['b'], F['flag']
+    sl0 = [slice(None)] * 3
+    sl1 = [slice(None)] * 3
+    sl0[axis] = slice(0, -1)
+    sl1[axis] = slice(1, None)
+    b0, b1 = b[tuple(sl0)], b[tuple(sl1)]
+    cross = flag[tuple(sl0)] & flag[tuple(sl1)] & ((b0 >= 0) != (b1 >= 0))
+    k, iz, ix = np.nonzero(cross)
+    c1 = (k, iz + (axis == 1), ix + (axis == 2))
+    c0 = (k, iz, ix)
+    t = b[c0] / (b[c0] - b[c1])
+    out = dict(k=k, iz=iz, ix=ix, t=t)
+    names = ('tau', 'bx', 'bz', 'bt', 'Tx', 'Tz', 'Tt')
+    for nm in names:
+        out[nm] = _interp(F[nm], c0, c1, t)
+    for nm in ('Vx', 'Vz', 'thetadot', 'pdx', 'pdz', 'v'):
+        out[nm] = _interp(S.vel[nm], c0, c1, t)
+    rho = np.broadcast_to(S.rho[None], b.shape)
+    out['rho'] = _interp(rho, c0, c1, t)
+    Th = lab['Th']
+    out['Th'] = Th[c0] + t * _wrap(Th[c1] - Th[c0])
+    return out
+
+
+def beam_centres(S, lab, F, axis, omega, beam_width):
+    """Complex Gaussian beam at each crossing of Gamma with a row (axis=2) or column (axis=1).
+
+    Dynamic ray tracing from the level sets (Eqs. 21-24): with k1 = grad b, k2 = grad vartheta and
+    e_t = (Vx, Vz, thetadot) (the null direction of both), the phase-space perturbation with
+    (db, dvartheta) = (1, kappa) is d = (k2 x e_t + kappa e_t x k1) / (e_t . (k1 x k2)).
+    kappa = 2 i |V_s| / (omega w0^2) makes the beam's wavefront Hessian at the source i 2/(omega w0^2)
+    (the complex initial data of Eq. 24, w0 the beam width).  With dx = (d_x, d_z) and
+    dp = p (pdot . dx) + dp/dtheta d_theta, the Cartesian Hessian solves M [dx, V] = [dp, pdot]
+    (Eq. 25's M = B C^-1) and the complex spreading is J = dx x V (det C of Eq. 26).
+    """
+    c = crossings(S, lab, F, axis)
+    if c['k'].size == 0:
+        return c, None
+    th = S.theta[c['k']]
+    n = np.stack([np.sin(th), np.cos(th)], -1)
+    nth_ = np.stack([np.cos(th), -np.sin(th)], -1)
+    V = np.stack([c['Vx'], c['Vz']], -1)
+    pdot = np.stack([c['pdx'], c['pdz']], -1)
+    v = c['v']
+    et = np.stack([c['Vx'], c['Vz'], c['thetadot']], -1)
+    k1 = np.stack([c['bx'], c['bz'], c['bt']], -1)
+    k2 = np.stack([c['Tx'], c['Tz'], c['Tt']], -1)
+    D = np.einsum('ni,ni->n', et, np.cross(k1, k2))
+    d_b = np.cross(k2, et) / D[:, None]
+    d_T = np.cross(et, k1) / D[:, None]
+    vs, _, Vsn, _ = _ch.source_quantities(S.a_s, c['Th'])
+    kappa = 2j * Vsn / (omega * beam_width ** 2)
+    d = d_b + kappa[:, None] * d_T
+    dx = d[:, :2]
+    dth = d[:, 2]
+    p = n / v[:, None]
+    v_th = np.einsum('ni,ni->n', nth_, V)
+    dp_dth = (nth_ * v[:, None] - n * v_th[:, None]) / (v ** 2)[:, None]
+    dp = p * np.einsum('ni,ni->n', pdot, dx)[:, None] + dp_dth * dth[:, None]
+    J = dx[:, 0] * V[:, 1] - dx[:, 1] * V[:, 0]
+    J_theta = d_T[:, 0] * V[:, 1] - d_T[:, 1] * V[:, 0]
+    Mxx = (dp[:, 0] * V[:, 1] - pdot[:, 0] * dx[:, 1]) / J
+    Mzz = (-dp[:, 1] * V[:, 0] + pdot[:, 1] * dx[:, 0]) / J
+    sigma = np.where(J_theta < 0, -1.0, 1.0)
+    amp = sigma * np.sqrt(S.rho_s * Vsn / (c['rho'] * J))
+    if axis == 2:
+        jac = c['Tt'] - c['Tx'] * c['bt'] / c['bx']
+        wpart = (V[:, 1] / np.hypot(V[:, 0], V[:, 1])) ** 2
+        M, pl = Mxx, p[:, 0]
+    else:
+        jac = c['Tt'] - c['Tz'] * c['bt'] / c['bz']
+        wpart = (V[:, 0] / np.hypot(V[:, 0], V[:, 1])) ** 2
+        M, pl = Mzz, p[:, 1]
+    weight = 1j * S.c_ref ** 2 / (4 * np.pi * vs ** 2)
+    coef = S.dth * np.abs(jac) * wpart * weight * amp
+    return c, dict(coef=coef, M=M, p=pl)
+
+
+def green(S, lab, omegas, beam_width):
+    """u(omega, z, x) complex128: Gaussian beams centred on Gamma summed over theta (Eq. 34).
+
+    Beams are centred where Gamma crosses the receiver's row (offset x0 - x_c along the row, the
+    paper's same-depth evaluation) and where it crosses the receiver's column (offset along the
+    column, for flat rays); the two are blended by the partition of unity g_z^2 + g_x^2 = 1 of the
+    unit group direction at the centre.  Each beam adds
+        dtheta |d vartheta_c / d theta| w c exp(i omega (tau_c + p_l delta + M_ll delta^2 / 2))
+    with c = i c_ref^2 / (4 pi v_s(vartheta)^2) sigma sqrt(rho_s |V_s| / (rho J)).
+    """
+    F = beam_fields(S, lab)
+    out = []
+    xg = S.hx * np.arange(S.nx)
+    zg = S.hz * np.arange(S.nz)
+    for om in omegas:
+        u = np.zeros((S.nz, S.nx), np.complex128)
+        for axis in (2, 1):
+            c, bc = beam_centres(S, lab, F, axis, om, beam_width)
+            if bc is None:
+                continue
+            if axis == 2:
+                xc = xg[c['ix']] + c['t'] * S.hx
+                delta = xg[None, :] - xc[:, None]
+            else:
+                zc = zg[c['iz']] + c['t'] * S.hz
+                delta = zg[None, :] - zc[:, None]
+            ph = np.exp(1j * om * (c['tau'][:, None] + bc['p'][:, None] * delta
+                                   + 0.5 * bc['M'][:, None] * delta ** 2))
+            contrib = bc['coef'][:, None] * ph
+            if axis == 2:
+                np.add.at(u, (c['iz'][:, None], np.arange(S.nx)[None, :]), contrib)
+            else:
+                np.add.at(u, (np.arange(S.nz)[None, :], c['ix'][:, None]), contrib)
+        out.append(u)
+    return np.stack(out)
+
+
+def arrivals(S, lab, kmax=8):
+    """count (nz, nx) uint8, T (nz, nx, kmax) float64, A (nz, nx, kmax) float64, overflow flag."""
+    F = beam_fields(S, lab)
+    v_r = S.vel['v']
+    rho_r = S.rho[None, :, :]
+    Acell = S.c_ref ** 2 * np.sqrt(S.rho_s / rho_r) / (
+        v_r * np.sqrt(8 * np.pi * F['Vsn'] * np.abs(F['bt'])))
+    b, tau, flag = F['b'], F['tau'], F['flag']
+    bn, taun, flagn, An = (np.roll(a, -1, axis=0) for a in (b, tau, flag, Acell))
+    cross = flag & flagn & ((b >= 0) != (bn >= 0))
+    nth, nz, nx = b.shape
+    count = np.zeros((nz, nx), np.uint8)
+    T = np.zeros((nz, nx, kmax))
+    A = np.zeros((nz, nx, kmax))
+    overflow = False
+    ks, izs, ixs = np.nonzero(cross)
+    t = b[ks, izs, ixs] / (b[ks, izs, ixs] - bn[ks, izs, ixs])
+    Tval = tau[ks, izs, ixs] + t * (taun[ks, izs, ixs] - tau[ks, izs, ixs])
+    Aval = Acell[ks, izs, ixs] + t * (An[ks, izs, ixs] - Acell[ks, izs, ixs])
+    order = np.lexsort((ks, Tval, ixs, izs))
+    per_node = {}
+    for j in order:
+        per_node.setdefault((izs[j], ixs[j]), []).append(j)
+    for (iz, ix), js in per_node.items():
+        if len(js) > kmax:
+            overflow = True
+        js = js[:kmax]
+        count[iz, ix] = len(js)
+        T[iz, ix, :len(js)] = Tval[js]
+        A[iz, ix, :len(js)] = Aval[js]
+    return count, T, A, overflow
+
+
+def min_abs_b_at_crossings(S, lab):
+    """Per node, the smallest |b| over the two cells of any counted crossing (inf if none)."""
+    F = beam_fields(S, lab)
+    b, flag = F['b'], F['flag']
+    bn, flagn = np.roll(b, -1, axis=0), np.roll(flag, -1, axis=0)
+    cross = flag & flagn & ((b >= 0) != (bn >= 0))
+    m = np.where(cross, np.minimum(np.abs(b), np.abs(bn)), np.inf)
+    return m.min(axis=0)

@@ -1,0 +1,293 @@
+"""Seeded synthetic media and workloads for the anisotropic Eulerian Gaussian beam solver.
+
+This module builds INPUTS only: elastic stiffness fields c_IJ(x) (21 Voigt constants per node,
+upper triangle row by row: C11 C12 C13 C14 C15 C16 C22 C23 C24 C25 C26 C33 C34 C35 C36 C44 C45
+C46 C55 C56 C66, in Pa), densities rho(x) (kg/m^3), grids, source positions, angular sampling,
+frequencies and step counts.  It holds none of the method's arithmetic (no Christoffel solve, no
+ray or level-set computation), so both the CUDA library and the independent FP64 oracle can take
+their inputs from here.
+
+Coordinates: x is the horizontal axis, z points down (depth); nodes sit at origin + i*h.  2-D grids
+are stored z-major with x fastest (node index = iz*nx + ix).
+
+Workloads (all synthetic, seeded with numpy PCG64):
+  * ``vti_homogeneous``    homogeneous VTI medium from Thomsen parameters (the 64x64x64 case)
+  * ``tti_heterogeneous``  2-D TTI medium: Vp0 = 2000 + z with two Gaussian +-15 % anomalies,
+                           Vs0 = Vp0/1.8, scalar epsilon/delta drawn once per medium, tilt from
+                           Gaussian-filtered noise scaled to +-30 deg, Gardner density
+  * ``isotropic_homogeneous``  Lame medium (closed-form pins)
+  * ``batched_instances``  uneven TTI instances (sizes, angle counts, frequencies drawn per instance)
+  * ``request_stream``     Poisson arrival stream of solve requests
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+# Voigt index of the tensor index pair (i, j), 0-based: 11->0 22->1 33->2 23->3 13->4 12->5
+_VOIGT = ((0, 5, 4), (5, 1, 3), (4, 3, 2))
+
+
+def voigt21_index(I: int, J: int) -> int:
+    """Position of C_IJ (0-based Voigt indices, any order) in the 21-entry upper-triangle list."""
+    if I > J:
+        I, J = J, I
+    return I * 6 - I * (I - 1) // 2 + (J - I)
+
+
+def thomsen_vti_voigt(vp0, vs0, eps, delta, rho, gamma=0.0):
+    """Stiffness (6x6 Voigt, Pa) of a VTI medium from Thomsen's parameters (Thomsen 1986).
+
+    c33 = rho Vp0^2, c55 = c44 = rho Vs0^2, c11 = c33 (1 + 2 eps), c66 = c44 (1 + 2 gamma),
+    (c13 + c55)^2 = (c33 - c55) (c33 (1 + 2 delta) - c55), c12 = c11 - 2 c66.
+    Broadcasts over array arguments; returns shape (..., 6, 6).
+    """
+    vp0, vs0, eps, delta, rho, gamma = np.broadcast_arrays(
+        *[np.asarray(a, dtype=np.float64) for a in (vp0, vs0, eps, delta, rho, gamma)])
+    c33 = rho * vp0 ** 2
+    c55 = rho * vs0 ** 2
+    c11 = c33 * (1.0 + 2.0 * eps)
+    c66 = c55 * (1.0 + 2.0 * gamma)
+    c13 = np.sqrt((c33 - c55) * (c33 * (1.0 + 2.0 * delta) - c55)) - c55
+    c12 = c11 - 2.0 * c66
+    C = np.zeros(vp0.shape + (6, 6))
+    C[..., 0, 0] = C[..., 1, 1] = c11
+    C[..., 2, 2] = c33
+    C[..., 0, 1] = C[..., 1, 0] = c12
+    C[..., 0, 2] = C[..., 2, 0] = C[..., 1, 2] = C[..., 2, 1] = c13
+    C[..., 3, 3] = C[..., 4, 4] = c55
+    C[..., 5, 5] = c66
+    return C
+
+
+def isotropic_voigt(lam, mu):
+    """Stiffness (6x6 Voigt) of an isotropic medium from the Lame constants."""
+    lam, mu = np.broadcast_arrays(np.asarray(lam, np.float64), np.asarray(mu, np.float64))
+    C = np.zeros(lam.shape + (6, 6))
+    for i in range(3):
+        for j in range(3):
+            C[..., i, j] = lam
+        C[..., i, i] = lam + 2 * mu
+        C[..., 3 + i, 3 + i] = mu
+    return C
+
+
+def _voigt_to_tensor(C):
+    c = np.empty(C.shape[:-2] + (3, 3, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    c[..., i, j, k, l] = C[..., _VOIGT[i][j], _VOIGT[k][l]]
+    return c
+
+
+def _tensor_to_voigt(c):
+    C = np.empty(c.shape[:-4] + (6, 6))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    C[..., _VOIGT[i][j], _VOIGT[k][l]] = c[..., i, j, k, l]
+    return C
+
+
+def rotate_voigt_about_y(C, tilt):
+    """Rotate a stiffness so that its z symmetry axis tilts by ``tilt`` (rad) from +z toward +x."""
+    tilt = np.asarray(tilt, np.float64)
+    ct, st = np.cos(tilt), np.sin(tilt)
+    R = np.zeros(tilt.shape + (3, 3))
+    R[..., 0, 0] = ct
+    R[..., 0, 2] = st
+    R[..., 1, 1] = 1.0
+    R[..., 2, 0] = -st
+    R[..., 2, 2] = ct
+    c = _voigt_to_tensor(C)
+    c = np.einsum('...ip,...jq,...kr,...ls,...pqrs->...ijkl', R, R, R, R, c, optimize=True)
+    return _tensor_to_voigt(c)
+
+
+def voigt_to_c21(C):
+    """(..., 6, 6) symmetric Voigt matrix -> (..., 21) upper triangle, row by row."""
+    iu = np.triu_indices(6)
+    return C[..., iu[0], iu[1]]
+
+
+def c21_to_voigt(c21):
+    """(..., 21) upper triangle -> (..., 6, 6) symmetric Voigt matrix."""
+    c21 = np.asarray(c21, np.float64)
+    C = np.zeros(c21.shape[:-1] + (6, 6))
+    iu = np.triu_indices(6)
+    C[..., iu[0], iu[1]] = c21
+    C[..., iu[1], iu[0]] = c21
+    return C
+
+
+def gardner_density(vp):
+    """Gardner's relation rho = 310 Vp^0.25 (kg/m^3, Vp in m/s)."""
+    return 310.0 * np.asarray(vp, np.float64) ** 0.25
+
+
+def _gaussian_filter(a, sigma_cells):
+    from scipy.ndimage import gaussian_filter
+    return gaussian_filter(a, sigma=sigma_cells, mode='reflect')
+
+
+@dataclass
+class Problem2D:
+    """One 2-D solve request: medium on an nz x nx node grid plus the source description."""
+    name: str
+    nx: int
+    nz: int
+    hx: float
+    hz: float
+    c21: np.ndarray           # (nz*nx, 21) float32, Pa
+    rho: np.ndarray           # (nz*nx,) float32, kg/m^3
+    xs: Tuple[float, float]   # source (x, z), m
+    n_theta: int
+    freqs: List[float]        # Hz
+    beam_width: float         # m
+    steps: int
+    cfl: float = 0.5
+    r0: Optional[float] = None   # frozen source-ball radius (m); default 2*max(hx, hz)
+    origin: Tuple[float, float] = (0.0, 0.0)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def omegas(self):
+        return [2.0 * math.pi * f for f in self.freqs]
+
+    @property
+    def ball_radius(self):
+        return self.r0 if self.r0 is not None else 2.0 * max(self.hx, self.hz)
+
+    @property
+    def cells(self):
+        return self.nx * self.nz * self.n_theta
+
+
+def _pack(C, rho):
+    c21 = voigt_to_c21(C).reshape(-1, 21).astype(np.float32)
+    return c21, np.asarray(rho, np.float64).reshape(-1).astype(np.float32)
+
+
+def vti_homogeneous(n=64, h=10.0, n_theta=64, steps=150, vp0=3000.0, vs0=1500.0, eps=0.20,
+                    delta=0.10, rho=2200.0, freqs=(15.0,), beam_width=50.0, cfl=0.5):
+    """Homogeneous VTI medium (Thomsen Vp0, Vs0, eps, delta, rho), source at node (n/2, n/2).
+
+    Defaults give the 64x64 grid at 10 m x 64 angles, 150 TVD-RK3 steps at CFL 0.5, 15 Hz, 50 m.
+    """
+    C = thomsen_vti_voigt(vp0, vs0, eps, delta, rho)
+    C = np.broadcast_to(C, (n, n, 6, 6))
+    c21, r = _pack(C, np.full((n, n), rho))
+    xs = ((n // 2) * h, (n // 2) * h)
+    return Problem2D('vti_homogeneous', n, n, h, h, c21, r, xs, n_theta, list(freqs), beam_width,
+                     steps, cfl, meta=dict(vp0=vp0, vs0=vs0, eps=eps, delta=delta, rho=rho))
+
+
+def isotropic_homogeneous(n=64, h=10.0, n_theta=64, steps=150, vp=3000.0, vs=1700.0, rho=2300.0,
+                          freqs=(15.0,), beam_width=50.0, cfl=0.5, xs=None):
+    """Homogeneous isotropic medium with P and S speeds vp, vs; source at the grid centre node."""
+    mu = rho * vs ** 2
+    lam = rho * vp ** 2 - 2 * mu
+    C = np.broadcast_to(isotropic_voigt(lam, mu), (n, n, 6, 6))
+    c21, r = _pack(C, np.full((n, n), rho))
+    if xs is None:
+        xs = ((n // 2) * h, (n // 2) * h)
+    return Problem2D('isotropic_homogeneous', n, n, h, h, c21, r, xs, n_theta, list(freqs),
+                     beam_width, steps, cfl, meta=dict(vp=vp, vs=vs, rho=rho))
+
+
+def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 40.0),
+                      beam_width=None, seed=2, cfl=0.5, length=None):
+    """2-D heterogeneous TTI medium.
+
+    Vp0 = (2000 + 1.0 z) (1 + 0.15 G1 - 0.15 G2), G_k Gaussians of sigma 300 m centred uniformly in
+    the middle 60 % of the domain; Vs0 = Vp0/1.8; epsilon ~ U[0, 0.25] and delta ~ U[-0.05, 0.15]
+    drawn once for the medium; tilt = white noise filtered by a Gaussian of sigma 200 m, scaled to a
+    maximum of 30 deg; Gardner density.  ``length`` (m) fixes the physical extent so reduced grids
+    (coarser h) describe the same medium; default n*h.  Source at the centre node.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = n * h if length is None else float(length)
+    h = L / n
+    x = np.arange(n) * h
+    z = np.arange(n) * h
+    Z, X = np.meshgrid(z, x, indexing='ij')
+    centres = rng.uniform(0.2 * L, 0.8 * L, size=(2, 2))
+    sig = 300.0
+    g = [np.exp(-((X - cx) ** 2 + (Z - cz) ** 2) / (2 * sig ** 2)) for cx, cz in centres]
+    vp0 = (2000.0 + 1.0 * Z) * (1.0 + 0.15 * g[0] - 0.15 * g[1])
+    vs0 = vp0 / 1.8
+    eps = rng.uniform(0.0, 0.25)
+    delta = rng.uniform(-0.05, 0.15)
+    noise = rng.standard_normal((n, n))
+    tilt = _gaussian_filter(noise, 200.0 / h)
+    tilt = tilt / np.max(np.abs(tilt)) * math.radians(30.0)
+    rho = gardner_density(vp0)
+    C = thomsen_vti_voigt(vp0, vs0, eps, delta, rho)
+    C = rotate_voigt_about_y(C, tilt)
+    c21, r = _pack(C, rho)
+    xs = ((n // 2) * h, (n // 2) * h)
+    if steps is None:
+        steps = tti_default_steps(n, h)
+    if beam_width is None:
+        beam_width = 50.0
+    return Problem2D('tti_heterogeneous', n, n, h, h, c21, r, xs, n_theta, list(freqs), beam_width,
+                     steps, cfl, meta=dict(seed=seed, eps=eps, delta=delta, centres=centres.tolist(),
+                                           length=L))
+
+
+def tti_default_steps(n, h):
+    """Pseudo-time steps for the TTI medium: 1.1 x (latest exit time of source rays) / dt.
+
+    The exit time (0.95 s for the 2560 m square) and the CFL-0.5 time step (which scales with h)
+    were measured for this medium family; the count is fixed here so that every run of the
+    workload advances the same number of steps.
+    """
+    t_exit = 0.95 * (n * h) / 2560.0
+    dt = 0.5 * h / 6700.0  # CFL-0.5 step bound: max(|Vx| + |Vz|) <= 6700 m/s in this family
+    return int(math.ceil(1.1 * t_exit / dt))
+
+
+def batched_instances(count=64, seed=3, n_range=(256, 1024), nth_range=(128, 512),
+                      f_range=(8.0, 40.0), h=5.0, size_scale=1.0):
+    """Uneven batch: instance i draws (seed 3 + i) grid n, angle count, 1-4 frequencies, TTI medium.
+
+    ``size_scale`` shrinks every drawn size (n and angle count) for reduced test versions.
+    """
+    out = []
+    for i in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed + i))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        nth = int(rng.integers(nth_range[0], nth_range[1] + 1))
+        nf = int(rng.integers(1, 5))
+        freqs = sorted(float(f) for f in rng.uniform(f_range[0], f_range[1], size=nf))
+        n = max(16, int(round(n * size_scale)) // 4 * 4)
+        nth = max(16, int(round(nth * size_scale)) // 2 * 2)
+        hh = h * (1.0 / size_scale if size_scale != 1.0 else 1.0)
+        p = tti_heterogeneous(n=n, h=hh, n_theta=nth, freqs=freqs, seed=1000 + seed + i)
+        p.name = f'batched_{i}'
+        out.append(p)
+    return out
+
+
+def request_stream(rate=200.0, duration=60.0, seed=4, max_requests=None):
+    """Poisson request stream: (arrival time s, kind, n_freq, freqs) with a 50/50 size mix."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    reqs = []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        kind = 'small' if rng.random() < 0.5 else 'large'
+        nf = int(rng.integers(1, 9))
+        freqs = sorted(float(f) for f in rng.uniform(8.0, 40.0, size=nf))
+        reqs.append((t, kind, nf, freqs))
+        if max_requests is not None and len(reqs) >= max_requests:
+            break
+    return reqs

@@ -1,0 +1,107 @@
+"""Pins for the oracle's Gaussian-beam superposition and arrival extraction (Eqs. 24-26, 33-35).
+
+The labels fed in here are the closed-form steady state of a homogeneous medium, so these tests
+check the superposition alone:
+* isotropic: u -> (i/4) H0^(1)(kr) with a relative L2 error that falls as kr grows, and the result
+  does not depend on the beam width to the same order (Gaussian-beam summation theory);
+* isotropic arrivals: exactly one arrival per node, T = r/v, A = |(i/4) H0| sqrt(omega) = sqrt(v/(8 pi r));
+* VTI: the far field of the exact plane-wave integral (stationary phase), traveltimes r/|V_g| along
+  the Thomsen group direction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthmedia
+from oracle import christoffel as CH
+from oracle import closed_forms as CF
+from oracle import liouville as L
+from oracle import superpose as SP
+
+
+def _exact_setup(problem):
+    S = L.Setup(problem)
+    x = np.arange(S.nx) * S.hx - S.xs[0]
+    z = np.arange(S.nz) * S.hz - S.xs[1]
+    Z, X = np.meshgrid(z, x, indexing='ij')
+    v, V, Vn, g = CH.source_quantities(S.a_s, S.theta)
+    p = np.stack([np.sin(S.theta) / v, np.cos(S.theta) / v], -1)
+    lab = CF.homogeneous_labels(S.theta, X, Z, g, p, S.r0, 1e4)
+    edge = np.minimum(np.minimum(X - X.min(), X.max() - X), np.minimum(Z - Z.min(), Z.max() - Z))
+    return S, lab, X, Z, edge
+
+
+@pytest.fixture(scope='module')
+def iso():
+    p = synthmedia.isotropic_homogeneous(n=128, h=10.0, n_theta=384, freqs=[60.0])
+    return (p,) + _exact_setup(p)
+
+
+def _band_errors(u, ref, kr, mask, bands):
+    out = []
+    for lo, hi in bands:
+        m = mask & (kr >= lo) & (kr < hi)
+        out.append(np.linalg.norm(u[m] - ref[m]) / np.linalg.norm(ref[m]))
+    return np.array(out)
+
+
+def test_isotropic_hankel_convergence(iso):
+    p, S, lab, X, Z, edge = iso
+    om = 2 * math.pi * 60.0
+    k = om / p.meta['vp']
+    r = np.hypot(X, Z)
+    ref = CF.hankel_green_2d(k, np.where(r > 0, r, 1.0))
+    u = SP.green(S, lab, [om], 100.0)[0]
+    bands = [(5, 10), (10, 20), (20, 40)]
+    err = _band_errors(u, ref, k * r, edge > 0.25 * 128 * 10.0, bands)
+    assert err[-1] < 0.02, err
+    assert np.all(np.diff(err) < 0), err
+
+
+def test_isotropic_beam_width_independence(iso):
+    p, S, lab, X, Z, edge = iso
+    om = 2 * math.pi * 60.0
+    k = om / p.meta['vp']
+    r = np.hypot(X, Z)
+    u1 = SP.green(S, lab, [om], 100.0)[0]
+    u2 = SP.green(S, lab, [om], 200.0)[0]
+    m = (edge > 0.25 * 128 * 10.0) & (k * r >= 20) & (k * r < 40)
+    assert np.linalg.norm(u1[m] - u2[m]) / np.linalg.norm(u1[m]) < 0.02
+
+
+def test_isotropic_arrivals(iso):
+    p, S, lab, X, Z, edge = iso
+    c = p.meta['vp']
+    cnt, T, A, overflow = SP.arrivals(S, lab)
+    r = np.hypot(X, Z)
+    m = r > 3 * S.r0
+    assert not overflow
+    assert np.all(cnt[m] == 1)
+    assert np.max(np.abs(T[..., 0][m] - r[m] / c) / (r[m] / c)) < 2e-4
+    Aref = np.sqrt(c / (8 * math.pi * r[m]))
+    assert np.max(np.abs(A[..., 0][m] - Aref) / Aref) < 2e-4
+
+
+@pytest.fixture(scope='module')
+def vti():
+    p = synthmedia.vti_homogeneous(n=128, h=10.0, n_theta=384, freqs=[60.0])
+    return (p,) + _exact_setup(p)
+
+
+def test_vti_far_field_matches_plane_wave_integral(vti):
+    p, S, lab, X, Z, edge = vti
+    m = p.meta
+    om = 2 * math.pi * 60.0
+    v_of = lambda th: CF.thomsen_vti_phase_velocity(th, m['vp0'], m['vs0'], m['eps'], m['delta'])
+    V_of = lambda th: CF.vti_group_velocity(th, m['vp0'], m['vs0'], m['eps'], m['delta'])[1:]
+    r = np.hypot(X, Z)
+    sel = (edge > 0.25 * 128 * 10.0) & (r > 350.0)
+    ref, T, _ = CF.homogeneous_go_green(X[sel], Z[sel], 0.0, 0.0, om, v_of, V_of, m['vp0'])
+    u = SP.green(S, lab, [om], 100.0)[0][sel]
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 0.03
+    cnt, Ta, A, _ = SP.arrivals(S, lab)
+    assert np.all(cnt[sel] == 1)
+    assert np.max(np.abs(Ta[..., 0][sel] - T) / T) < 2e-4
+    Aref = np.abs(ref) * math.sqrt(om)
+    assert np.max(np.abs(A[..., 0][sel] - Aref) / Aref) < 2e-3
