@@ -1,0 +1,324 @@
+"""Benchmark: phase-space cell-updates/s of the anisotropic Eulerian Gaussian beam solver on GB300.
+
+One step = one whole solve of the workload through the C ABI: medium upload and validation,
+characteristic velocities and initial level sets (egb_medium, egb_source), the pseudo-time evolution
+(egb_evolve: HJ-WENO3 / TVD-RK3 on every phase-space cell for the workload's step count) and the
+Gaussian-beam superposition with arrival extraction at every frequency (egb_superpose).
+
+Default workload: the heterogeneous 2-D TTI medium on a 512 x 512 grid at 5 m with 256 phase
+angles, frequencies 10, 20 and 40 Hz, single source at the centre.  `value` is cell-updates per
+second with the medium already resident in HBM; `e2e` is the same metric through the C ABI with
+host buffers (medium uploaded from pinned host memory, every output copied back, inside the timed
+region).  The state (1.3 GB per copy) is far larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl egb|reference]
+Under torchrun every rank runs its own replica (independent solves, no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthmedia  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+# Algorithmic bytes of the stencil per cell-update: the 2-D state (3 FP32 labels + 8-byte tau) read
+# and written once per TVD-RK3 step (40 B) plus the stored characteristic velocities read once
+# (Vx, Vz, dtheta/dt: 12 B).
+ALGO_BYTES_PER_CELL_UPDATE = 52.0
+
+
+def workload(name):
+    if name == 'tti512':
+        return synthmedia.tti_heterogeneous(n=512, h=5.0, n_theta=256, freqs=(10.0, 20.0, 40.0))
+    if name == 'vti64':
+        return synthmedia.vti_homogeneous()
+    if name == 'tti128':
+        return synthmedia.tti_heterogeneous(n=128, n_theta=128, length=2560.0, steps=400,
+                                            freqs=(10.0, 20.0, 40.0))
+    raise ValueError(name)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d['hbm_gbs']), 'measured'
+    return HBM_FALLBACK_GBS, 'fallback'
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ('clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,'
+             'clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,'
+             'clocks_event_reasons.sw_power_cap')
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.index), f'--query-gpu={q}', '--format=csv,noheader,nounits',
+                 '-lms', '200'], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(',')]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['no samples']}
+        sm = [float(s[0]) for s in self.samples if s[0].replace('.', '', 1).isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace('.', '', 1).isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == 'Active'})
+        return {'sm_mhz': float(np.median(sm)) if sm else None,
+                'sm_max_mhz': max(mx) if mx else None, 'reasons': reasons, 'samples': len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+def run_egb(args):
+    import torch
+    import paper_2006_11945_gb300 as egb
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+    p = workload(args.workload)
+    steps_evolve = p.steps if args.evolve_steps is None else args.evolve_steps
+    stream = torch.cuda.Stream()
+    ctx = egb.Context(local, stream.cuda_stream)
+    nodes = p.nx * p.nz
+    c21_d = torch.from_numpy(np.ascontiguousarray(p.c21)).cuda()
+    rho_d = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    c21_h = torch.from_numpy(np.ascontiguousarray(p.c21)).pin_memory()
+    rho_h = torch.from_numpy(np.ascontiguousarray(p.rho)).pin_memory()
+    no, kmax = len(p.freqs), 8
+    u_d = torch.empty((no, p.nz, p.nx, 2), dtype=torch.float32, device='cuda')
+    cnt_d = torch.empty((p.nz, p.nx), dtype=torch.uint8, device='cuda')
+    T_d = torch.empty((p.nz, p.nx, kmax), dtype=torch.float64, device='cuda')
+    A_d = torch.empty((p.nz, p.nx, kmax), dtype=torch.float32, device='cuda')
+    u_h = torch.empty((no, p.nz, p.nx, 2), dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty((p.nz, p.nx), dtype=torch.uint8).pin_memory()
+    T_h = torch.empty((p.nz, p.nx, kmax), dtype=torch.float64).pin_memory()
+    A_h = torch.empty((p.nz, p.nx, kmax), dtype=torch.float32).pin_memory()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evolve_ms = []
+
+    def solve(host):
+        n = (p.nx, 1, p.nz)
+        hs = (p.hx, 1.0, p.hz)
+        org = (p.origin[0], 0.0, p.origin[1])
+        c21, rho = (c21_h, rho_h) if host else (c21_d, rho_d)
+        m = egb.egb_medium(ctx.h, n, hs, org, c21, rho)
+        s = egb.egb_source(ctx.h, m, (p.xs[0], 0.0, p.xs[1]), p.omegas, p.beam_width, p.n_theta, 0.0)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+        egb.egb_evolve(ctx.h, s, steps_evolve, p.cfl)
+        with torch.cuda.stream(stream):
+            ev1.record(stream)
+        if host:
+            egb.egb_superpose(ctx.h, s, u_h, cnt_h, T_h, A_h, kmax)
+        else:
+            egb.egb_superpose(ctx.h, s, u_d, cnt_d, T_d, A_d, kmax)
+        egb.egb_sync(ctx.h)
+        evolve_ms.append(ev0.elapsed_time(ev1))
+        info = egb.egb_get_solve_info(ctx.h, s)
+        egb.egb_release(ctx.h, s)
+        egb.egb_release(ctx.h, m)
+        return info
+
+    def timed(host, K, W):
+        for _ in range(W):
+            solve(host)
+        evolve_ms.clear()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+        for _ in range(K):
+            info = solve(host)
+        with torch.cuda.stream(stream):
+            t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        if dist is not None:
+            t = torch.tensor([ms], device='cuda')
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, info
+
+    with ClockSampler(local) as clk:
+        ms, info = timed(False, args.steps, args.warmup)
+    evolve_avg_ms = float(np.mean(evolve_ms))
+    e2e_ms, _ = timed(True, max(1, args.steps), 1)
+    cells = info['cells']
+    cu_per_solve = cells * steps_evolve
+    per_step_ms = ms / args.steps
+    value = ws * cu_per_solve * args.steps / (ms / 1e3)
+    e2e_value = ws * cu_per_solve * max(1, args.steps) / (e2e_ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    launch_ms = evolve_avg_ms / (3 * steps_evolve)
+    achieved = ALGO_BYTES_PER_CELL_UPDATE * cells / 3.0 / (launch_ms / 1e3) / 1e9
+    launches = 2 + 3 + 3 * steps_evolve + 5
+    h2d = p.c21.nbytes + p.rho.nbytes
+    d2h = u_h.numel() * 4 + cnt_h.numel() + T_h.numel() * 8 + A_h.numel() * 4
+    line = {
+        'metric': 'phase-space cell-updates/s',
+        'value': value,
+        'unit': 'cell-updates/s',
+        'n_gpus': ws,
+        'steps': args.steps,
+        'warmup': args.warmup,
+        'ms_per_step': per_step_ms,
+        'higher_is_better': True,
+        'scaling': 'weak',
+        'vs_baseline': None,
+        'dtype': 'f32 (double-float tau and phase)',
+        'data': 'synthetic (seeded TTI medium)',
+        'config': {'workload': f'{p.name} {p.nx}x{p.nz} at {p.hx:g} m x {p.n_theta} angles, '
+                               f'{steps_evolve} TVD-RK3 steps, {len(p.freqs)} frequencies',
+                   'cells': cells, 'evolve_steps': steps_evolve, 'freqs_hz': p.freqs,
+                   'parallelism': f'replicas x{ws}', 'l2': 'state (1.3 GB) larger than L2, no flush'},
+        'solves_per_s': ws * args.steps / (ms / 1e3),
+        'beam_point_sums_per_s': ws * args.steps * p.nx * p.nz * p.n_theta * len(p.freqs) / (ms / 1e3),
+        'e2e': {'value': e2e_value, 'unit': 'cell-updates/s', 'h2d_bytes_per_step': int(h2d),
+                'd2h_bytes_per_step': int(d2h)},
+        'roofline': {'bound': 'hbm', 'kernel': 'k_rk3_stage', 'achieved': achieved, 'peak': peak,
+                     'unit': 'GB/s', 'frac': achieved / peak, 'traffic': None,
+                     'peak_kind': peak_kind, 'launch_ms': launch_ms},
+        'gpu_launches': launches * args.steps,
+        'clocks': clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line['cpu_baseline'] = cpu_baseline(p, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(p, sub=128):
+    """A sub-block of the workload's medium (same spacing and angle count) for the CPU oracle."""
+    n = min(sub, p.nx)
+    c21 = p.c21.reshape(p.nz, p.nx, 21)[:n, :n].reshape(-1, 21).copy()
+    rho = p.rho.reshape(p.nz, p.nx)[:n, :n].reshape(-1).copy()
+    q = synthmedia.Problem2D(p.name + '_sample', n, n, p.hx, p.hz, c21, rho,
+                             ((n // 2) * p.hx, (n // 2) * p.hz), p.n_theta, p.freqs, p.beam_width,
+                             p.steps, p.cfl)
+    return q
+
+
+def cpu_baseline(p, budget_s=20.0):
+    """Time the FP64 oracle's evolution on a bounded sample of the workload (host cores)."""
+    from oracle import liouville as OL
+    q = _oracle_sample(p)
+    S = OL.Setup(q)
+    st = S.initial_state()
+    t = time.perf_counter()
+    S2, st, dt = OL.evolve(q, steps=1, S=S, state=st)
+    one = time.perf_counter() - t
+    steps = max(1, min(200, int(budget_s / max(one, 1e-3))))
+    t = time.perf_counter()
+    OL.evolve(q, steps=steps, S=S, state=st)
+    el = time.perf_counter() - t
+    cores = int(os.environ.get('OMP_NUM_THREADS', os.cpu_count() or 1))
+    return {'value': q.cells * steps / el, 'unit': 'cell-updates/s', 'cores': cores, 'kind': 'oracle',
+            'sample': f'{q.nx}x{q.nz}x{q.n_theta} sub-block of the workload medium, {steps} TVD-RK3 '
+                      f'steps of the float64 oracle (compiled loop), evolution only'}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    q = _oracle_sample(p)
+    from oracle import liouville as OL
+    S = OL.Setup(q)
+    st = S.initial_state()
+    per = 2
+    for _ in range(args.warmup):
+        _, st, _ = OL.evolve(q, steps=per, S=S, state=st)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        _, st, _ = OL.evolve(q, steps=per, S=S, state=st)
+    el = time.perf_counter() - t
+    value = q.cells * per * args.steps / el
+    cores = int(os.environ.get('OMP_NUM_THREADS', os.cpu_count() or 1))
+    sample = f'{q.nx}x{q.nz}x{q.n_theta} sub-block of the workload medium, {per} TVD-RK3 steps per step'
+    print(json.dumps({
+        'impl': 'reference', 'metric': 'phase-space cell-updates/s', 'value': value,
+        'unit': 'cell-updates/s', 'n_gpus': ws, 'steps': args.steps, 'warmup': args.warmup,
+        'ms_per_step': el / args.steps * 1e3, 'higher_is_better': True, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded TTI medium)',
+        'config': {'workload': f'{p.name} {p.nx}x{p.nz} at {p.hx:g} m x {p.n_theta} angles (oracle sample)'},
+        'cpu_baseline': {'value': value, 'unit': 'cell-updates/s', 'cores': cores, 'kind': 'oracle',
+                         'sample': sample},
+        'e2e': {'value': value, 'unit': 'cell-updates/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=3)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
+    ap.add_argument('--workload', default='tti512', choices=['tti512', 'tti128', 'vti64'])
+    ap.add_argument('--evolve-steps', type=int, default=None)
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--cpu-seconds', type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == 'reference':
+        run_reference(args)
+    else:
+        run_egb(args)
+
+
+if __name__ == '__main__':
+    main()

@@ -1,0 +1,155 @@
+/* egb.h — C ABI of the GB300 anisotropic Eulerian Gaussian beam library (libegb.so).
+ *
+ * The library computes frequency-domain qP Green's functions of a point source in a 2-D
+ * anisotropic, heterogeneous elastic medium with the Eulerian Gaussian beam method of X. Huang,
+ * "Eulerian Gaussian beams for high frequency wave propagation in inhomogeneous media of arbitrary
+ * anisotropy" (arXiv 2006.11945).  The calls follow the paper's statement of the problem:
+ *
+ *   egb_medium    c_ijkl(x), rho(x)                         (Sec. 2, Eqs. 1, 4, 5)
+ *   egb_source    point source x_s, frequencies, beam width (Sec. 4, Eq. 20; Eq. 24)
+ *   egb_evolve    level sets advected through phase space   (Sec. 4, Eqs. 16, 19)
+ *   egb_superpose Gaussian beams summed over the source manifold into u(x, omega), plus the
+ *                 traveltime and amplitude of every arrival  (Sec. 5, Eqs. 25-26, 33-35)
+ *
+ * Conventions (apply to every call):
+ *   - Status: every call returns egb_status; EGB_OK is 0.  No C++ exception crosses the ABI.
+ *     egb_last_error(ctx) returns a NUL-terminated description of the last failure (owned by ctx,
+ *     valid until the next call on ctx).
+ *   - Asynchrony: work is enqueued on the CUDA stream given to egb_create.  Errors detected on the
+ *     device (non-positive-definite medium, non-finite values, arrival overflow) are latched and
+ *     returned by the next egb_sync (or by the next call that synchronises).
+ *   - Pointers: array arguments may be host or device pointers (the library asks the CUDA runtime
+ *     which).  Host outputs are written before the call returns; device outputs are written in
+ *     stream order.
+ *   - Ownership: the library owns media and solves (device resident until egb_release or
+ *     egb_destroy).  The caller owns every buffer it passes.
+ *   - Units: SI.  omega in rad/s, lengths in m, stiffness in Pa, density in kg/m^3.
+ *   - Grids: 2-D node grids, x horizontal, z down, nodes at origin + i*h, stored z-major with x
+ *     fastest (node = iz*nx + ix).  Phase angles theta_k = 2 pi k / n_theta, from +z toward +x.
+ *   - Threading: calls on one context are serialised by an internal mutex.
+ */
+#ifndef EGB_H
+#define EGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EGB_OK = 0,
+    EGB_E_INVALID = 1,          /* bad argument (sizes, pointers, unknown id, unsupported dim) */
+    EGB_E_NOT_PD = 2,           /* stiffness not positive definite at some node */
+    EGB_E_NOMEM = 3,            /* not enough free device memory (admission refusal) */
+    EGB_E_CUDA = 4,             /* CUDA runtime error */
+    EGB_E_TIMEOUT = 5,          /* a bounded device wait gave up */
+    EGB_E_NUMERIC = 6,          /* non-finite value produced */
+    EGB_E_ARRIVAL_OVERFLOW = 7, /* more arrivals (or beam centres) than the caller's capacity */
+    EGB_E_BUSY = 8              /* object in use */
+} egb_status;
+
+typedef struct egb_ctx egb_ctx;
+typedef uint64_t egb_medium_id;
+typedef uint64_t egb_solve_id;
+
+enum { EGB_FP32_PHASE64 = 0, EGB_FP64 = 1 };
+
+typedef struct {
+    int precision;      /* EGB_FP32_PHASE64: FP32 stencil/superposition with double-float tau and
+                           phase; EGB_FP64: the plain all-FP64 form (comparison baseline) */
+    int store_velocity; /* 1: characteristic velocities stored once per solve (the only mode) */
+    int checked;        /* reserved, 0 */
+} egb_opts;
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL for
+ * the legacy default stream).  opts may be NULL (defaults: EGB_FP32_PHASE64, stored velocity).
+ * Errors: EGB_E_INVALID (NULL out), EGB_E_CUDA (device cannot be selected). */
+egb_status egb_create(egb_ctx **out, int device, void *cuda_stream, const egb_opts *opts);
+
+/* Release every medium and solve of the context and the context itself. */
+egb_status egb_destroy(egb_ctx *ctx);
+
+/* Upload a medium (Sec. 2: a_ijkl = c_ijkl / rho, Eq. 5).
+ *   dim      2 (3-D media are rejected with EGB_E_INVALID)
+ *   n        {nx, ny, nz}; ny ignored for dim 2; nx, nz >= 5
+ *   h        {hx, hy, hz} node spacing (m, > 0); origin {ox, oy, oz} (m)
+ *   c21      [nz*nx][21] float32 stiffness per node, Voigt upper triangle row by row
+ *            (C11 C12 C13 C14 C15 C16 C22 ... C66), Pa; host or device
+ *   rho      [nz*nx] float32 density per node (> 0), host or device
+ *   out      receives the medium id
+ * The device validates positive definiteness per node (6x6 Cholesky); failure is reported as
+ * EGB_E_NOT_PD by the next synchronising call.  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_CUDA. */
+egb_status egb_medium(egb_ctx *ctx, int dim, const int n[3], const double h[3],
+                      const double origin[3], const float *c21, const float *rho,
+                      egb_medium_id *out);
+
+/* Create a solve: a point source in a medium (Sec. 4, Eq. 20 initial data).
+ *   xs          {x, y, z} source position (m), inside the grid
+ *   n_omega     number of angular frequencies (1..64); omega[n_omega] rad/s (> 0), host memory
+ *   beam_width  w0 (m, > 0): the Gaussian beams' 1/e half-width along the wavefront at the source
+ *               (the complex initial data of Eq. 24)
+ *   n_ang       {n_theta, unused}: phase-angle samples (8..4096)
+ *   r0          radius (m) of the frozen source ball; <= 0 selects 2*max(hx, hz)
+ * Allocates the phase-space state (about 3 x 20 + 24 bytes per cell) after checking free device
+ * memory (EGB_E_NOMEM otherwise), computes the characteristic velocities (Eqs. 3-12), the time
+ * step bound and the initial level sets.  Synchronises the context stream once (to read the CFL
+ * bound).  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_NOT_PD (medium failed validation), EGB_E_CUDA. */
+egb_status egb_source(egb_ctx *ctx, egb_medium_id medium, const double xs[3], int n_omega,
+                      const double *omega, double beam_width, const int n_ang[2], double r0,
+                      egb_solve_id *out);
+
+/* Advance the level sets `steps` TVD-RK3 steps (HJ-WENO3 in x, z, theta) at Courant number cfl
+ * (0 < cfl <= 1); dt = cfl / max(|Vx|/hx + |Vz|/hz + |dtheta/dt|/dtheta).  Steps compose: calling
+ * twice with s1 and s2 equals one call with s1 + s2.  Asynchronous.  Errors: EGB_E_INVALID. */
+egb_status egb_evolve(egb_ctx *ctx, egb_solve_id solve, int steps, double cfl);
+
+/* Superpose the Gaussian beams (Eqs. 25-26, 33-35) and extract arrivals.
+ *   u_out   complex64 [n_omega][nz][nx] (interleaved re, im), or NULL
+ *   count   uint8 [nz][nx] number of arrivals kept per node, or NULL
+ *   T       float64 [nz][nx][kmax] traveltimes (s), ascending; unused slots 0; or NULL
+ *   A       float32 [nz][nx][kmax] geometrical amplitudes |u| sqrt(omega); unused 0; or NULL
+ *   kmax    capacity per node (1..32) when count/T/A are given
+ * Output scaling: rho_s c_ref^2 times the scalar qP Green's function, c_ref the source phase
+ * velocity along +z; a homogeneous isotropic medium gives (i/4) H0^(1)(k r); phase exp(+i omega T)
+ * (Eq. 2).  Nodes with more than kmax arrivals keep the kmax earliest and latch
+ * EGB_E_ARRIVAL_OVERFLOW.  Errors: EGB_E_INVALID, EGB_E_CUDA. */
+egb_status egb_superpose(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t *count, double *T,
+                         float *A, int kmax);
+
+/* Wait for the context stream and report latched device errors (then clear them). */
+egb_status egb_sync(egb_ctx *ctx);
+
+/* Free a medium or a solve (ids are unique across both kinds).  Errors: EGB_E_INVALID (unknown),
+ * EGB_E_BUSY (a medium that still has solves). */
+egb_status egb_release(egb_ctx *ctx, uint64_t id);
+
+const char *egb_last_error(egb_ctx *ctx);
+
+/* Read-only facts about a solve (not a step of the method; for callers that report throughput). */
+typedef struct {
+    int nx, nz, n_theta, n_omega;
+    int steps_done;
+    double dt;             /* pseudo-time step of the last egb_evolve (s) */
+    double max_rate;       /* max(|Vx|/hx + |Vz|/hz + |thetadot|/dtheta) (1/s) */
+    double c_ref;          /* source qP phase velocity along +z (m/s) */
+    uint64_t cells;        /* nx * nz * n_theta */
+    uint64_t device_bytes; /* device memory held by the solve */
+} egb_solve_info;
+
+egb_status egb_get_solve_info(egb_ctx *ctx, egb_solve_id solve, egb_solve_info *out);
+
+/* Copy the level sets of a solve to the caller: out = [4][n_theta][nz][nx] float64 holding
+ * Yx, Yz (position label minus x_s), vartheta, tau, host or device.  Synchronous.  For tests and
+ * diagnostics (the state otherwise stays on the device). */
+egb_status egb_read_state(egb_ctx *ctx, egb_solve_id solve, double *out);
+
+/* Copy the characteristic velocities: out = [6][n_theta][nz][nx] float32 holding Vx, Vz,
+ * dtheta/dt, v (phase velocity), dp_x/dt, dp_z/dt.  Synchronous. */
+egb_status egb_read_velocity(egb_ctx *ctx, egb_solve_id solve, float *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EGB_H */

@@ -1,0 +1,423 @@
+// C ABI of libegb: contexts, media and solves (declared in include/egb.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "egb_internal.cuh"
+
+using namespace egb;
+
+struct egb_ctx : public Ctx {};
+
+namespace {
+
+egb_status fail(egb_ctx *c, egb_status st, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+egb_status cuda_fail(egb_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, EGB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t free_bytes() {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    return fr;
+}
+
+void free_solve(Solve *s) {
+    for (auto &p : s->state) cudaFree(p);
+    cudaFree(s->vel);
+    cudaFree(s->ball);
+    cudaFree(s->src);
+    cudaFree(s->scratch);
+    delete s;
+}
+
+void free_medium(Medium *m) {
+    cudaFree(m->a);
+    cudaFree(m->dadx);
+    cudaFree(m->dadz);
+    cudaFree(m->rho);
+    delete m;
+}
+
+egb_status latched(egb_ctx *c) {
+    unsigned bits = 0;
+    cudaError_t e = cudaMemcpyAsync(&bits, c->d_err, sizeof bits, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronisation");
+    if (bits) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
+        cudaStreamSynchronize(c->stream);
+        if (bits & DeviceErrors::NOT_PD) return fail(c, EGB_E_NOT_PD, "medium not positive definite (or non-finite / non-positive density) at some node");
+        if (bits & DeviceErrors::TIMEOUT) return fail(c, EGB_E_TIMEOUT, "bounded device wait expired");
+        if (bits & DeviceErrors::NUMERIC) return fail(c, EGB_E_NUMERIC, "non-finite value produced");
+        if (bits & DeviceErrors::OVERFLOW) return fail(c, EGB_E_ARRIVAL_OVERFLOW, "more arrivals or beam centres than the capacity");
+    }
+    return EGB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+egb_status egb_create(egb_ctx **out, int device, void *cuda_stream, const egb_opts *opts) {
+    if (!out) return EGB_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return EGB_E_CUDA;
+    }
+    egb_ctx *c = new egb_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->opts = opts ? *opts : egb_opts{EGB_FP32_PHASE64, 1, 0};
+    DeviceGuard dg(device);
+    if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return EGB_E_CUDA;
+    }
+    *out = c;
+    return EGB_OK;
+}
+
+egb_status egb_destroy(egb_ctx *c) {
+    if (!c) return EGB_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        DeviceGuard dg(c->device);
+        cudaStreamSynchronize(c->stream);
+        for (auto &kv : c->solves) free_solve(kv.second);
+        for (auto &kv : c->media) free_medium(kv.second);
+        c->solves.clear();
+        c->media.clear();
+        cudaFree(c->d_err);
+    }
+    delete c;
+    return EGB_OK;
+}
+
+const char *egb_last_error(egb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], const double origin[3],
+                      const float *c21, const float *rho, egb_medium_id *out) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!n || !h || !origin || !c21 || !rho || !out) return fail(c, EGB_E_INVALID, "null argument");
+    if (dim != 2) return fail(c, EGB_E_INVALID, "only dim = 2 media are supported");
+    if (n[0] < 5 || n[2] < 5) return fail(c, EGB_E_INVALID, "nx and nz must be >= 5");
+    if (!(h[0] > 0) || !(h[2] > 0)) return fail(c, EGB_E_INVALID, "spacings must be > 0");
+    DeviceGuard dg(c->device);
+    Medium *m = new Medium();
+    m->nx = n[0];
+    m->nz = n[2];
+    m->hx = h[0];
+    m->hz = h[2];
+    m->ox = origin[0];
+    m->oz = origin[2];
+    size_t nodes = (size_t)m->nx * m->nz;
+    m->bytes = nodes * 4 * (21 * 3 + 1);
+    if (m->bytes + (64u << 20) > free_bytes()) { delete m; return fail(c, EGB_E_NOMEM, "medium needs %zu bytes", m->bytes); }
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&m->a, nodes * 21 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->dadx, nodes * 21 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->dadz, nodes * 21 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->rho, nodes * 4);
+    if (e != cudaSuccess) { cudaGetLastError(); free_medium(m); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the medium"); }
+    const float *dc = c21, *dr = rho;
+    float *tc = nullptr, *tr = nullptr;
+    if (!is_device_ptr(c21)) {
+        e = cudaMalloc(&tc, nodes * 21 * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tc, c21, nodes * 21 * 4, cudaMemcpyHostToDevice, c->stream);
+        dc = tc;
+    }
+    if (e == cudaSuccess && !is_device_ptr(rho)) {
+        e = cudaMalloc(&tr, nodes * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tr, rho, nodes * 4, cudaMemcpyHostToDevice, c->stream);
+        dr = tr;
+    }
+    if (e == cudaSuccess) e = launch_medium_prep(*m, dc, dr, c->d_err, c->stream);
+    if (e == cudaSuccess && (tc || tr)) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tc);
+    cudaFree(tr);
+    if (e != cudaSuccess) { free_medium(m); return cuda_fail(c, e, "medium upload"); }
+    uint64_t id = c->next_id++;
+    c->media[id] = m;
+    *out = id;
+    return EGB_OK;
+}
+
+egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_omega,
+                      const double *omega, double beam_width, const int n_ang[2], double r0,
+                      egb_solve_id *out) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->media.find(mid);
+    if (it == c->media.end()) return fail(c, EGB_E_INVALID, "unknown medium id");
+    if (!xs || !omega || !n_ang || !out) return fail(c, EGB_E_INVALID, "null argument");
+    if (n_omega < 1 || n_omega > 64) return fail(c, EGB_E_INVALID, "n_omega must be in 1..64");
+    for (int i = 0; i < n_omega; ++i)
+        if (!(omega[i] > 0)) return fail(c, EGB_E_INVALID, "omega must be > 0");
+    if (!(beam_width > 0)) return fail(c, EGB_E_INVALID, "beam width must be > 0");
+    int nth = n_ang[0];
+    if (nth < 8 || nth > 4096) return fail(c, EGB_E_INVALID, "n_theta must be in 8..4096");
+    Medium *m = it->second;
+    double x0 = m->ox, x1 = m->ox + (m->nx - 1) * m->hx, z0 = m->oz, z1 = m->oz + (m->nz - 1) * m->hz;
+    if (!(xs[0] >= x0 && xs[0] <= x1 && xs[2] >= z0 && xs[2] <= z1))
+        return fail(c, EGB_E_INVALID, "source outside the grid");
+    DeviceGuard dg(c->device);
+    egb_status pre = latched(c);  // medium validation result
+    if (pre != EGB_OK) return pre;
+    Solve *s = new Solve();
+    s->medium_id = mid;
+    s->m = m;
+    Grid2D &g = s->g;
+    g.nx = m->nx;
+    g.nz = m->nz;
+    g.nth = nth;
+    g.pitch = ((m->nx + 2 * XPAD) + 3) / 4 * 4;
+    g.plane = (int64_t)(g.nz + 2 * ZPAD) * g.pitch;
+    g.field = g.plane * nth;
+    g.hx = m->hx;
+    g.hz = m->hz;
+    g.ox = m->ox;
+    g.oz = m->oz;
+    g.dth = 2.0 * M_PI / nth;
+    s->xs = xs[0];
+    s->zs = xs[2];
+    s->r0 = r0 > 0 ? r0 : 2.0 * (m->hx > m->hz ? m->hx : m->hz);
+    s->w0 = beam_width;
+    s->omega.assign(omega, omega + n_omega);
+    size_t cells = (size_t)nth * g.nx * g.nz;
+    size_t state_b = (size_t)NFIELD * g.field * 4;
+    s->bytes = 3 * state_b + cells * 6 * 4 + g.nz * 8 + (24 + 4 * nth) * 4;
+    if (s->bytes + (256u << 20) > free_bytes()) {
+        delete s;
+        return fail(c, EGB_E_NOMEM, "solve needs %zu bytes of device memory", (size_t)(s->bytes));
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &p : s->state)
+        if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
+    if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 6 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->ball, g.nz * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
+    if (e != cudaSuccess) { cudaGetLastError(); free_solve(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
+    // frozen source ball: per row the ix range with (x - xs)^2 + (z - zs)^2 <= r0^2 (FP64)
+    std::vector<int2> ball(g.nz);
+    for (int iz = 0; iz < g.nz; ++iz) {
+        double dz = (g.oz + iz * g.hz) - s->zs;
+        int lo = g.nx, hi = -1;
+        for (int ix = 0; ix < g.nx; ++ix) {
+            double dx = (g.ox + ix * g.hx) - s->xs;
+            if (dz * dz + dx * dx <= s->r0 * s->r0) {
+                if (ix < lo) lo = ix;
+                hi = ix;
+            }
+        }
+        ball[iz] = make_int2(lo, hi);
+    }
+    float *d_rate = nullptr;
+    e = cudaMalloc(&d_rate, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_rate, 0, 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ball, ball.data(), g.nz * sizeof(int2), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_solve_setup(*s, c->d_err, d_rate, c->stream);
+    if (e == cudaSuccess) e = launch_init_state(*s, c->stream);
+    float rate = 0, cref = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rate, d_rate, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cref, s->src + 22, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_rate);
+    if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "solve setup"); }
+    if (!(rate > 0) || !std::isfinite(rate)) { free_solve(s); return fail(c, EGB_E_NUMERIC, "invalid characteristic speeds"); }
+    s->max_rate = rate;
+    s->c_ref = cref;
+    s->cur = 0;
+    uint64_t id = c->next_id++;
+    c->solves[id] = s;
+    m->solves++;
+    *out = id;
+    return EGB_OK;
+}
+
+egb_status egb_evolve(egb_ctx *c, egb_solve_id sid, int steps, double cfl) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    if (steps < 0 || !(cfl > 0) || cfl > 1) return fail(c, EGB_E_INVALID, "steps >= 0 and 0 < cfl <= 1 required");
+    Solve *s = it->second;
+    DeviceGuard dg(c->device);
+    s->dt = cfl / s->max_rate;
+    for (int i = 0; i < steps; ++i) {
+        cudaError_t e = launch_rk3_step(*s, (float)s->dt, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "evolve launch");
+    }
+    s->steps += steps;
+    return EGB_OK;
+}
+
+egb_status egb_superpose(egb_ctx *c, egb_solve_id sid, void *u_out, uint8_t *count, double *T,
+                         float *A, int kmax) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    bool want_arr = count || T || A;
+    if (want_arr && (kmax < 1 || kmax > 32)) return fail(c, EGB_E_INVALID, "kmax must be in 1..32");
+    Solve *s = it->second;
+    DeviceGuard dg(c->device);
+    size_t need = superpose_scratch_bytes(*s);
+    cudaError_t e = cudaSuccess;
+    if (s->scratch_bytes < need) {
+        cudaFree(s->scratch);
+        s->scratch = nullptr;
+        s->scratch_bytes = 0;
+        e = cudaMalloc(&s->scratch, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, EGB_E_NOMEM, "superposition scratch (%zu bytes)", need); }
+        s->scratch_bytes = need;
+    }
+    const Grid2D &g = s->g;
+    size_t nodes = (size_t)g.nx * g.nz;
+    size_t ub = s->omega.size() * nodes * 8;
+    // outputs: device pointers are written directly, host pointers through temporaries
+    void *du = u_out;
+    uint8_t *dc = count;
+    double *dT = T;
+    float *dA = A;
+    bool hu = u_out && !is_device_ptr(u_out), hc = count && !is_device_ptr(count);
+    bool hT = T && !is_device_ptr(T), hA = A && !is_device_ptr(A);
+    if (hu) e = cudaMalloc(&du, ub);
+    if (e == cudaSuccess && hc) e = cudaMalloc(&dc, nodes);
+    if (e == cudaSuccess && hT) e = cudaMalloc(&dT, nodes * kmax * 8);
+    if (e == cudaSuccess && hA) e = cudaMalloc(&dA, nodes * kmax * 4);
+    if (e == cudaSuccess)
+        e = launch_superpose(*s, (float2 *)du, dc, dT, dA, kmax, c->d_err, c->stream);
+    if (e == cudaSuccess && hu) e = cudaMemcpyAsync(u_out, du, ub, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hc) e = cudaMemcpyAsync(count, dc, nodes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hT) e = cudaMemcpyAsync(T, dT, nodes * kmax * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hA) e = cudaMemcpyAsync(A, dA, nodes * kmax * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && (hu || hc || hT || hA)) e = cudaStreamSynchronize(c->stream);
+    if (hu) cudaFree(du);
+    if (hc) cudaFree(dc);
+    if (hT) cudaFree(dT);
+    if (hA) cudaFree(dA);
+    if (e != cudaSuccess) return cuda_fail(c, e, "superpose");
+    return EGB_OK;
+}
+
+egb_status egb_sync(egb_ctx *c) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    return latched(c);
+}
+
+egb_status egb_release(egb_ctx *c, uint64_t id) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard dg(c->device);
+    auto is = c->solves.find(id);
+    if (is != c->solves.end()) {
+        cudaStreamSynchronize(c->stream);
+        is->second->m->solves--;
+        free_solve(is->second);
+        c->solves.erase(is);
+        return EGB_OK;
+    }
+    auto im = c->media.find(id);
+    if (im != c->media.end()) {
+        if (im->second->solves > 0) return fail(c, EGB_E_BUSY, "medium still has solves");
+        cudaStreamSynchronize(c->stream);
+        free_medium(im->second);
+        c->media.erase(im);
+        return EGB_OK;
+    }
+    return fail(c, EGB_E_INVALID, "unknown id");
+}
+
+egb_status egb_get_solve_info(egb_ctx *c, egb_solve_id sid, egb_solve_info *out) {
+    if (!c || !out) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    Solve *s = it->second;
+    out->nx = s->g.nx;
+    out->nz = s->g.nz;
+    out->n_theta = s->g.nth;
+    out->n_omega = (int)s->omega.size();
+    out->steps_done = s->steps;
+    out->dt = s->dt;
+    out->max_rate = s->max_rate;
+    out->c_ref = s->c_ref;
+    out->cells = (uint64_t)s->g.nth * s->g.nx * s->g.nz;
+    out->device_bytes = s->bytes + s->scratch_bytes;
+    return EGB_OK;
+}
+
+egb_status egb_read_state(egb_ctx *c, egb_solve_id sid, double *out) {
+    if (!c || !out) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    Solve *s = it->second;
+    DeviceGuard dg(c->device);
+    size_t bytes = (size_t)4 * s->g.nth * s->g.nx * s->g.nz * 8;
+    double *d = out;
+    bool host = !is_device_ptr(out);
+    cudaError_t e = cudaSuccess;
+    if (host) e = cudaMalloc(&d, bytes);
+    if (e == cudaSuccess) e = launch_read_state(*s, d, c->stream);
+    if (e == cudaSuccess && host) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (host) cudaFree(d);
+    return e == cudaSuccess ? EGB_OK : cuda_fail(c, e, "read state");
+}
+
+egb_status egb_read_velocity(egb_ctx *c, egb_solve_id sid, float *out) {
+    if (!c || !out) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    Solve *s = it->second;
+    DeviceGuard dg(c->device);
+    size_t bytes = (size_t)6 * s->g.nth * s->g.nx * s->g.nz * 4;
+    cudaError_t e = cudaMemcpyAsync(out, s->vel, bytes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? EGB_OK : cuda_fail(c, e, "read velocity");
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Internal declarations shared by the CUDA translation units of libegb (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/egb.h"
+
+namespace egb {
+
+// ---------------------------------------------------------------------------------------------
+// Layout of the 2-D phase-space state.
+// Every field is a stack of n_theta planes; a plane has (nz + 4) rows of `pitch` floats.  Row r
+// holds depth index iz = r - 2 (two ghost rows on each side); column c holds ix = c - XPAD
+// (XPAD = 4 keeps the interior 16-byte aligned; columns XPAD-2, XPAD-1 and XPAD+nx, XPAD+nx+1 are
+// the ghost layers).  Ghosts hold the initial data permanently (Dirichlet inflow).
+// Fields: 0 Yx, 1 Yz (position label minus x_s), 2 vartheta, 3 tau_hi, 4 tau_lo (double-float tau).
+// ---------------------------------------------------------------------------------------------
+constexpr int XPAD = 4;
+constexpr int ZPAD = 2;
+constexpr int NFIELD = 5;
+constexpr int KC = 16;  // beam centres kept per grid line and angle
+
+struct Grid2D {
+    int nx, nz, nth;
+    int pitch;        // floats per padded row
+    int64_t plane;    // floats per padded plane = (nz + 4) * pitch
+    int64_t field;    // floats per field = nth * plane
+    double hx, hz, ox, oz, dth;
+};
+
+__host__ __device__ inline int64_t pidx(const Grid2D &g, int k, int iz, int ix) {
+    return (int64_t)k * g.plane + (int64_t)(iz + ZPAD) * g.pitch + (ix + XPAD);
+}
+__host__ __device__ inline int64_t cidx(const Grid2D &g, int k, int iz, int ix) {
+    return ((int64_t)k * g.nz + iz) * g.nx + ix;
+}
+
+// Voigt bookkeeping: 21 constants stored as the upper triangle of the 6x6 matrix, row by row.
+__host__ __device__ constexpr int voigt(int i, int j) { return i == j ? i : 6 - i - j; }
+__host__ __device__ constexpr int tri21(int I, int J) {
+    return I <= J ? I * 6 - I * (I - 1) / 2 + (J - I) : J * 6 - J * (J - 1) / 2 + (I - J);
+}
+__host__ __device__ constexpr int aidx(int i, int j, int k, int l) {
+    return tri21(voigt(i, j), voigt(k, l));
+}
+
+// Double-float helpers (Knuth's TwoSum and Dekker's FastTwoSum).
+struct ff { float hi, lo; };
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+// (hi, lo) + d  ->  renormalised double-float
+__device__ __forceinline__ ff ff_add_f(float hi, float lo, float d) {
+    ff s = two_sum(hi, d);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, lo));
+}
+
+struct DeviceErrors {  // bits latched by kernels, read by egb_sync
+    enum : unsigned { NOT_PD = 1u, NUMERIC = 2u, OVERFLOW = 4u, TIMEOUT = 8u };
+};
+
+// ---------------------------------------------------------------------------------------------
+// Host-side objects
+// ---------------------------------------------------------------------------------------------
+struct Medium {
+    int nx, nz;
+    double hx, hz, ox, oz;
+    float *a = nullptr;     // [21][nz][nx]  a = c / rho
+    float *dadx = nullptr;  // [21][nz][nx]
+    float *dadz = nullptr;  // [21][nz][nx]
+    float *rho = nullptr;   // [nz][nx]
+    int solves = 0;
+    size_t bytes = 0;
+};
+
+struct Solve {
+    uint64_t medium_id;
+    Medium *m;
+    Grid2D g;
+    double xs, zs, r0, w0;
+    std::vector<double> omega;
+    float *state[3] = {nullptr, nullptr, nullptr};  // three padded buffers of NFIELD fields
+    int cur = 0;                                     // buffer holding u^n
+    float *vel = nullptr;   // [6][nth][nz][nx]: Vx, Vz, thetadot, v, pdx, pdz
+    int2 *ball = nullptr;   // [nz] frozen ix range per row (lo > hi: none)
+    float *src = nullptr;   // source block: a_s[21], rho_s, c_ref, then [nth] x (psx, psz)
+    float *scratch = nullptr;  // superposition scratch (lazily sized)
+    size_t scratch_bytes = 0;
+    double max_rate = 0, dt = 0, c_ref = 0;
+    int steps = 0;
+    size_t bytes = 0;
+};
+
+struct Ctx {
+    int device;
+    cudaStream_t stream;
+    egb_opts opts;
+    std::mutex mu;
+    std::string err;
+    uint64_t next_id = 1;
+    std::unordered_map<uint64_t, Medium *> media;
+    std::unordered_map<uint64_t, Solve *> solves;
+    unsigned *d_err = nullptr;  // device error bits
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const float *rho_dev,
+                               unsigned *d_err, cudaStream_t s);
+cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, cudaStream_t s);
+cudaError_t launch_init_state(const Solve &sv, cudaStream_t s);
+cudaError_t launch_rk3_step(Solve &sv, float dt, cudaStream_t s);
+cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
+                             float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
+size_t superpose_scratch_bytes(const Solve &sv);
+cudaError_t launch_read_state(const Solve &sv, double *out_dev, cudaStream_t s);
+
+}  // namespace egb

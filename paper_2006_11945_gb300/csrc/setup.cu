@@ -1,0 +1,232 @@
+// Medium preparation, characteristic velocities, source tables and initial level sets.
+//
+// Sec. 2, Eq. 5: a_ijkl = c_ijkl / rho (per node), with second-order central differences for its
+// gradient (second-order one-sided at the grid edges) and a 6x6 Cholesky positive-definiteness
+// check.  Eqs. 3-12: per phase cell the qP eigenpair and the ray velocities (christoffel.cuh).
+// Eq. 20 (generalised to a frozen source ball): labels Y = x - x_s, vartheta = theta,
+// tau = p_s(theta) . (x - x_s) on every cell, ghosts included.
+#include "christoffel.cuh"
+
+namespace egb {
+
+// ------------------------------- medium --------------------------------------------------------
+__global__ void k_medium_a(int nodes, const float *__restrict__ c21, const float *__restrict__ rho,
+                           float *__restrict__ a, unsigned *err) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+    float r = rho[n];
+    float c[21];
+    bool ok = isfinite(r) && r > 0.f;
+#pragma unroll
+    for (int q = 0; q < 21; ++q) {
+        c[q] = c21[(int64_t)n * 21 + q];
+        ok = ok && isfinite(c[q]);
+        a[(int64_t)q * nodes + n] = c[q] / r;
+    }
+    // Cholesky of the 6x6 Voigt matrix (scaled by its largest diagonal entry)
+    float L[6][6];
+    float sc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sc = fmaxf(sc, fabsf(c[tri21(i, i)]));
+    sc = sc > 0.f ? 1.f / sc : 1.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float d = c[tri21(j, j)] * sc;
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        ok = ok && d > 0.f;
+        float ljj = sqrtf(fmaxf(d, 1e-30f));
+        L[j][j] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            float t = c[tri21(i, j)] * sc;
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / ljj;
+        }
+    }
+    if (!ok) atomicOr(err, DeviceErrors::NOT_PD);
+}
+
+__global__ void k_medium_grad(int nx, int nz, float ihx, float ihz, const float *__restrict__ a,
+                              float *__restrict__ dadx, float *__restrict__ dadz) {
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y;
+    int q = blockIdx.z;
+    if (ix >= nx) return;
+    const float *f = a + (int64_t)q * nx * nz + (int64_t)iz * nx;
+    float gx;
+    if (ix == 0) gx = (4.f * (f[1] - f[0]) - (f[2] - f[0])) * 0.5f * ihx;
+    else if (ix == nx - 1) gx = (4.f * (f[nx - 1] - f[nx - 2]) - (f[nx - 1] - f[nx - 3])) * 0.5f * ihx;
+    else gx = (f[ix + 1] - f[ix - 1]) * 0.5f * ihx;
+    const float *col = a + (int64_t)q * nx * nz + ix;
+    float gz;
+    if (iz == 0) gz = (4.f * (col[nx] - col[0]) - (col[2 * nx] - col[0])) * 0.5f * ihz;
+    else if (iz == nz - 1)
+        gz = (4.f * (col[(int64_t)(nz - 1) * nx] - col[(int64_t)(nz - 2) * nx]) -
+              (col[(int64_t)(nz - 1) * nx] - col[(int64_t)(nz - 3) * nx])) * 0.5f * ihz;
+    else gz = (col[(int64_t)(iz + 1) * nx] - col[(int64_t)(iz - 1) * nx]) * 0.5f * ihz;
+    int64_t o = (int64_t)q * nx * nz + (int64_t)iz * nx + ix;
+    dadx[o] = gx;
+    dadz[o] = gz;
+}
+
+cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const float *rho_dev,
+                               unsigned *d_err, cudaStream_t s) {
+    int nodes = m.nx * m.nz;
+    k_medium_a<<<(nodes + 127) / 128, 128, 0, s>>>(nodes, c21_dev, rho_dev, m.a, d_err);
+    dim3 grid((m.nx + 127) / 128, m.nz, 21);
+    k_medium_grad<<<grid, 128, 0, s>>>(m.nx, m.nz, (float)(1.0 / m.hx), (float)(1.0 / m.hz), m.a,
+                                       m.dadx, m.dadz);
+    cudaMemcpyAsync(m.rho, rho_dev, sizeof(float) * nodes, cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+// ------------------------------- source block ---------------------------------------------------
+// src layout (floats): [0,21) a_s, [21] rho_s, [22] c_ref, [23] pad,
+//                      [24 + 2k] psx_k, [25 + 2k] psz_k, [24 + 2 nth + 2k] sin, cos theta_k
+__host__ __device__ inline int src_ps(int k) { return 24 + 2 * k; }
+__host__ __device__ inline int src_sc(int nth, int k) { return 24 + 2 * nth + 2 * k; }
+
+__device__ void bilinear_weights(const Medium &m, double xs, double zs, int &ix, int &iz, double &tx,
+                                 double &tz) {
+    double fx = (xs - m.ox) / m.hx, fz = (zs - m.oz) / m.hz;
+    ix = (int)floor(fx);
+    iz = (int)floor(fz);
+    ix = ix < 0 ? 0 : (ix > m.nx - 2 ? m.nx - 2 : ix);
+    iz = iz < 0 ? 0 : (iz > m.nz - 2 ? m.nz - 2 : iz);
+    tx = fx - ix;
+    tz = fz - iz;
+}
+
+__global__ void k_source(Medium m, double xs, double zs, int nth, float *src) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int ix, iz;
+    double tx, tz;
+    bilinear_weights(m, xs, zs, ix, iz, tx, tz);
+    int nodes = m.nx * m.nz;
+    int n00 = iz * m.nx + ix;
+    auto interp = [&](const float *f) {
+        return (float)((1 - tz) * ((1 - tx) * f[n00] + tx * f[n00 + 1]) +
+                       tz * ((1 - tx) * f[n00 + m.nx] + tx * f[n00 + m.nx + 1]));
+    };
+    float as[21];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) as[q] = interp(m.a + (int64_t)q * nodes);
+    if (k == 0) {
+        for (int q = 0; q < 21; ++q) src[q] = as[q];
+        src[21] = interp(m.rho);
+        SrcVel r0 = source_velocity(as, 0.f, 1.f);
+        src[22] = r0.v;
+        src[23] = 0.f;
+    }
+    if (k >= nth) return;
+    double th = 2.0 * M_PI * k / nth;
+    float s = (float)sin(th), c = (float)cos(th);
+    SrcVel r = source_velocity(as, s, c);
+    src[src_ps(k)] = s / r.v;
+    src[src_ps(k) + 1] = c / r.v;
+    src[src_sc(nth, k)] = s;
+    src[src_sc(nth, k) + 1] = c;
+}
+
+// ------------------------------- velocities ------------------------------------------------------
+__global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, float *__restrict__ vel,
+                           float *rate_out) {
+    int node = blockIdx.x * blockDim.x + threadIdx.x;
+    int nodes = g.nx * g.nz;
+    float rmax = 0.f;
+    if (node < nodes) {
+        float a[21], dx[21], dz[21];
+#pragma unroll
+        for (int q = 0; q < 21; ++q) {
+            a[q] = m.a[(int64_t)q * nodes + node];
+            dx[q] = m.dadx[(int64_t)q * nodes + node];
+            dz[q] = m.dadz[(int64_t)q * nodes + node];
+        }
+        int64_t cells = (int64_t)g.nth * nodes;
+        float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
+        for (int k = 0; k < g.nth; ++k) {
+            float s = src[src_sc(g.nth, k)], c = src[src_sc(g.nth, k) + 1];
+            RayVel r = ray_velocity2d(a, dx, dz, s, c);
+            int64_t o = (int64_t)k * nodes + node;
+            vel[o] = r.Vx;
+            vel[cells + o] = r.Vz;
+            vel[2 * cells + o] = r.td;
+            vel[3 * cells + o] = r.v;
+            vel[4 * cells + o] = r.pdx;
+            vel[5 * cells + o] = r.pdz;
+            rmax = fmaxf(rmax, fabsf(r.Vx) * ihx + fabsf(r.Vz) * ihz + fabsf(r.td) * idth);
+        }
+    }
+    // block max -> one atomic per block (non-negative floats order like their bit patterns)
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    __shared__ float wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wmax[w]);
+        atomicMax((int *)rate_out, __float_as_int(b));
+    }
+}
+
+cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, cudaStream_t s) {
+    (void)d_err;
+    k_source<<<(sv.g.nth + 127) / 128, 128, 0, s>>>(*sv.m, sv.xs, sv.zs, sv.g.nth, sv.src);
+    int nodes = sv.g.nx * sv.g.nz;
+    k_velocity<<<(nodes + 127) / 128, 128, 0, s>>>(*sv.m, sv.g, sv.src, sv.vel, d_rate);
+    return cudaGetLastError();
+}
+
+// ------------------------------- initial level sets ---------------------------------------------
+__global__ void k_init(Grid2D g, double xs, double zs, const float *__restrict__ src, float *b0,
+                       float *b1, float *b2) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    int k = blockIdx.z;
+    if (c >= g.pitch) return;
+    int ix = c - XPAD, iz = r - ZPAD;
+    double x = g.ox + ix * g.hx - xs;
+    double z = g.oz + iz * g.hz - zs;
+    double th = 2.0 * M_PI * k / g.nth;
+    double tau = (double)src[src_ps(k)] * x + (double)src[src_ps(k) + 1] * z;
+    float hi = (float)tau;
+    float lo = (float)(tau - (double)hi);
+    float vals[NFIELD] = {(float)x, (float)z, (float)th, hi, lo};
+    int64_t o = (int64_t)k * g.plane + (int64_t)r * g.pitch + c;
+#pragma unroll
+    for (int f = 0; f < NFIELD; ++f) {
+        b0[f * g.field + o] = vals[f];
+        b1[f * g.field + o] = vals[f];
+        b2[f * g.field + o] = vals[f];
+    }
+}
+
+cudaError_t launch_init_state(const Solve &sv, cudaStream_t s) {
+    dim3 grid((sv.g.pitch + 127) / 128, sv.g.nz + 2 * ZPAD, sv.g.nth);
+    k_init<<<grid, 128, 0, s>>>(sv.g, sv.xs, sv.zs, sv.src, sv.state[0], sv.state[1], sv.state[2]);
+    return cudaGetLastError();
+}
+
+// ------------------------------- state read-back -------------------------------------------------
+__global__ void k_read_state(Grid2D g, const float *__restrict__ st, double *out) {
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y, k = blockIdx.z;
+    if (ix >= g.nx) return;
+    int64_t p = pidx(g, k, iz, ix);
+    int64_t cells = (int64_t)g.nth * g.nx * g.nz;
+    int64_t o = cidx(g, k, iz, ix);
+    out[o] = st[p];
+    out[cells + o] = st[g.field + p];
+    out[2 * cells + o] = st[2 * g.field + p];
+    out[3 * cells + o] = (double)st[3 * g.field + p] + (double)st[4 * g.field + p];
+}
+
+cudaError_t launch_read_state(const Solve &sv, double *out_dev, cudaStream_t s) {
+    dim3 grid((sv.g.nx + 127) / 128, sv.g.nz, sv.g.nth);
+    k_read_state<<<grid, 128, 0, s>>>(sv.g, sv.state[sv.cur], out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace egb

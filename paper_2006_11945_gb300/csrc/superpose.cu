@@ -1,0 +1,436 @@
+// Gaussian-beam superposition over the source manifold and arrival extraction.
+//
+// Sec. 5.  Gamma = {b = 0} (Eq. 35) with b = (Y - x_s) x g_s(vartheta) the impact parameter of the
+// ray at the source (g_s the unit group direction of the source medium, 2-D cross product
+// a x b = a_x b_z - a_z b_x); a cell counts as ball-origin when |Y - x_s| <= r0 + 2h.
+//
+//  k_beam_fields   per cell: b, ball-origin flag, |V_s(vartheta)|                     (Eq. 35)
+//  k_centres       per grid line (row: fixed z, or column: fixed x) and angle: every sign change of
+//                  b between flagged neighbours is a beam centre; its level-set gradients give the
+//                  dynamic ray tracing (Eqs. 21-24) -> complex Hessian M (Eq. 25), spreading det C
+//                  and amplitude (Eq. 26), weight (Eq. 33), and exp(i omega tau) with omega tau
+//                  reduced mod 2 pi in double-float (Cody & Waite's split-constant reduction)
+//  k_sum           per receiver: sum over angles of the beams centred on its row (offset along x:
+//                  the paper's same-depth evaluation) and on its column (offset along z, for flat
+//                  rays), blended by g_z^2 + g_x^2 = 1                                      (Eq. 34)
+//  k_arrivals      per receiver: sign changes of b along theta -> traveltime and geometrical
+//                  amplitude of every arrival, late arrivals included
+#include "christoffel.cuh"
+
+namespace egb {
+
+struct SupArgs {
+    Grid2D g;
+    const float *st;    // padded state (u^n)
+    const float *vel;   // [6][cells]
+    const float *rho;   // [nz][nx]
+    const float *src;   // source block
+    float *B, *VSN;     // [cells]
+    uint8_t *FL;        // [cells]
+    // beam centres: rows [nth][nz][KC], columns [nth][nx][KC]
+    int *rcnt, *ccnt;
+    float *rpos, *cpos, *rp, *cp;
+    float4 *rdat, *cdat;  // [n_omega][line slots]: E.re, E.im, M.re, M.im
+    int n_omega;
+    const double *omega_dev;
+    float w0, r0, flag_r2;
+    float C1, C2, C3;     // 2 pi split for the range reduction
+    unsigned *err;
+};
+
+__device__ __forceinline__ float wrap_angle(float d) {
+    const float two_pi = 6.28318530717958647692f;
+    return d - two_pi * rintf(d * 0.159154943091895335769f);
+}
+
+__global__ void k_beam_fields(SupArgs A) {
+    const Grid2D &g = A.g;
+    __shared__ float as[21];
+    if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
+    __syncthreads();
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y, k = blockIdx.z;
+    if (ix >= g.nx) return;
+    int64_t p = pidx(g, k, iz, ix);
+    float yx = A.st[p], yz = A.st[g.field + p], th = A.st[2 * g.field + p];
+    float s, c;
+    sincosf(th, &s, &c);
+    SrcVel r = source_velocity(as, s, c);
+    float inv = 1.f / r.Vn;
+    float b = yx * (r.Vz * inv) - yz * (r.Vx * inv);
+    int64_t o = cidx(g, k, iz, ix);
+    A.B[o] = b;
+    A.VSN[o] = r.Vn;
+    A.FL[o] = (yx * yx + yz * yz) <= A.flag_r2 ? 1 : 0;
+}
+
+// Gradient along x (dir 0) or z (dir 1) of a cell field F[cells], second order, one-sided at edges.
+__device__ __forceinline__ float grad_line(const float *F, int64_t o, int i, int n, int64_t stride,
+                                           float ih) {
+    if (i == 0) return (4.f * (F[o + stride] - F[o]) - (F[o + 2 * stride] - F[o])) * 0.5f * ih;
+    if (i == n - 1) return (4.f * (F[o] - F[o - stride]) - (F[o] - F[o - 2 * stride])) * 0.5f * ih;
+    return (F[o + stride] - F[o - stride]) * 0.5f * ih;
+}
+// Same on the padded angle label, differences wrapped.
+__device__ __forceinline__ float grad_line_angle(const float *F, int64_t p, int i, int n,
+                                                 int64_t stride, float ih) {
+    if (i == 0)
+        return (4.f * wrap_angle(F[p + stride] - F[p]) - wrap_angle(F[p + 2 * stride] - F[p])) * 0.5f * ih;
+    if (i == n - 1)
+        return (4.f * wrap_angle(F[p] - F[p - stride]) - wrap_angle(F[p] - F[p - 2 * stride])) * 0.5f * ih;
+    return wrap_angle(F[p + stride] - F[p - stride]) * 0.5f * ih;
+}
+
+struct CellData {
+    float bx, bz, bt, tx, tz, tt;
+    float Vx, Vz, td, pdx, pdz, v, rho, th;
+    float tau_hi, tau_lo;
+};
+
+__device__ CellData load_cell(const SupArgs &A, int k, int iz, int ix) {
+    const Grid2D &g = A.g;
+    CellData d;
+    int64_t o = cidx(g, k, iz, ix);
+    int64_t plane = (int64_t)g.nx * g.nz;
+    float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
+    d.bx = grad_line(A.B, o, ix, g.nx, 1, ihx);
+    d.bz = grad_line(A.B, o, iz, g.nz, g.nx, ihz);
+    int kp = (k + 1) % g.nth, km = (k - 1 + g.nth) % g.nth;
+    d.bt = (A.B[cidx(g, kp, iz, ix)] - A.B[cidx(g, km, iz, ix)]) * 0.5f * idth;
+    const float *Th = A.st + 2 * g.field;
+    int64_t p = pidx(g, k, iz, ix);
+    d.tx = grad_line_angle(Th, p, ix, g.nx, 1, ihx);
+    d.tz = grad_line_angle(Th, p, iz, g.nz, g.pitch, ihz);
+    d.tt = wrap_angle(Th[pidx(g, kp, iz, ix)] - Th[pidx(g, km, iz, ix)]) * 0.5f * idth;
+    d.th = Th[p];
+    int64_t cells = (int64_t)g.nth * plane;
+    d.Vx = A.vel[o];
+    d.Vz = A.vel[cells + o];
+    d.td = A.vel[2 * cells + o];
+    d.v = A.vel[3 * cells + o];
+    d.pdx = A.vel[4 * cells + o];
+    d.pdz = A.vel[5 * cells + o];
+    d.rho = A.rho[(int64_t)iz * g.nx + ix];
+    d.tau_hi = A.st[3 * g.field + p];
+    d.tau_lo = A.st[4 * g.field + p];
+    return d;
+}
+
+struct cf { float re, im; };
+__device__ __forceinline__ cf cmul(cf a, cf b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cf cdiv(cf a, cf b) {
+    float d = 1.f / (b.re * b.re + b.im * b.im);
+    return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
+}
+__device__ __forceinline__ cf csqrt_pr(cf z) {  // principal branch
+    float r = hypotf(z.re, z.im);
+    float re = sqrtf(fmaxf(0.5f * (r + z.re), 0.f));
+    float im = copysignf(sqrtf(fmaxf(0.5f * (r - z.re), 0.f)), z.im);
+    return {re, im};
+}
+
+// omega * tau mod 2 pi with tau = hi + lo, omega = ohi + olo (double-float), Cody-Waite reduction.
+__device__ __forceinline__ float phase_mod(float ohi, float olo, float thi, float tlo, float C1,
+                                           float C2, float C3) {
+    float p = ohi * thi;
+    float e = fmaf(ohi, thi, -p);
+    e = fmaf(ohi, tlo, e);
+    e = fmaf(olo, thi, e);
+    float k = rintf(p * 0.159154943091895335769f);
+    float r = fmaf(-k, C1, p);
+    r = fmaf(-k, C2, r);
+    r = fmaf(-k, C3, r);
+    return r + e;
+}
+
+// One line (row if ROW, else column) per thread; up to KC beam centres.
+template <bool ROW>
+__global__ void k_centres(SupArgs A) {
+    const Grid2D &g = A.g;
+    __shared__ float as[21];
+    if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
+    __syncthreads();
+    int line = blockIdx.x * blockDim.x + threadIdx.x;
+    int nl = ROW ? g.nz : g.nx;
+    int len = ROW ? g.nx : g.nz;
+    int k = blockIdx.y;
+    if (line >= nl) return;
+    int64_t slot0 = ((int64_t)k * nl + line) * KC;
+    int64_t lines_total = (int64_t)g.nth * nl * KC;
+    float rho_s = A.src[21], c_ref = A.src[22];
+    float sth, cth;
+    {
+        double th = 2.0 * M_PI * k / g.nth;
+        sth = (float)sin(th);
+        cth = (float)cos(th);
+    }
+    float h = ROW ? (float)g.hx : (float)g.hz;
+    int cnt = 0;
+    for (int i = 0; i + 1 < len; ++i) {
+        int iz0 = ROW ? line : i, ix0 = ROW ? i : line;
+        int iz1 = ROW ? line : i + 1, ix1 = ROW ? i + 1 : line;
+        int64_t o0 = cidx(g, k, iz0, ix0), o1 = cidx(g, k, iz1, ix1);
+        if (!(A.FL[o0] && A.FL[o1])) continue;
+        float b0 = A.B[o0], b1 = A.B[o1];
+        if ((b0 >= 0.f) == (b1 >= 0.f)) continue;
+        if (cnt >= KC) { atomicOr(A.err, DeviceErrors::OVERFLOW); break; }
+        float t = b0 / (b0 - b1);
+        CellData c0 = load_cell(A, k, iz0, ix0), c1 = load_cell(A, k, iz1, ix1);
+        auto L = [t](float a, float b) { return a + t * (b - a); };
+        float bx = L(c0.bx, c1.bx), bz = L(c0.bz, c1.bz), bt = L(c0.bt, c1.bt);
+        float tx = L(c0.tx, c1.tx), tz = L(c0.tz, c1.tz), tt = L(c0.tt, c1.tt);
+        float Vx = L(c0.Vx, c1.Vx), Vz = L(c0.Vz, c1.Vz), td = L(c0.td, c1.td);
+        float pdx = L(c0.pdx, c1.pdx), pdz = L(c0.pdz, c1.pdz), v = L(c0.v, c1.v);
+        float rho = L(c0.rho, c1.rho);
+        float thc = c0.th + t * wrap_angle(c1.th - c0.th);
+        float tau_hi = c0.tau_hi;
+        float tau_lo = c0.tau_lo + t * ((c1.tau_hi - c0.tau_hi) + (c1.tau_lo - c0.tau_lo));
+        // dynamic ray tracing from the label gradients
+        float e[3] = {Vx, Vz, td}, k1[3] = {bx, bz, bt}, k2[3] = {tx, tz, tt};
+        float x12[3] = {k1[1] * k2[2] - k1[2] * k2[1], k1[2] * k2[0] - k1[0] * k2[2], k1[0] * k2[1] - k1[1] * k2[0]};
+        float D = e[0] * x12[0] + e[1] * x12[1] + e[2] * x12[2];
+        float iD = 1.f / D;
+        float db[3] = {(k2[1] * e[2] - k2[2] * e[1]) * iD, (k2[2] * e[0] - k2[0] * e[2]) * iD,
+                       (k2[0] * e[1] - k2[1] * e[0]) * iD};
+        float dT[3] = {(e[1] * k1[2] - e[2] * k1[1]) * iD, (e[2] * k1[0] - e[0] * k1[2]) * iD,
+                       (e[0] * k1[1] - e[1] * k1[0]) * iD};
+        float ss, cs;
+        sincosf(thc, &ss, &cs);
+        SrcVel sv = source_velocity(as, ss, cs);
+        float pxl = sth / v, pzl = cth / v;
+        float vth = cth * Vx - sth * Vz;
+        float iv2 = 1.f / (v * v);
+        float dpth_x = (cth * v - sth * vth) * iv2, dpth_z = (-sth * v - cth * vth) * iv2;
+        float Jt = dT[0] * Vz - dT[1] * Vx;
+        float sigma = Jt < 0.f ? -1.f : 1.f;
+        float Vn = sqrtf(Vx * Vx + Vz * Vz);
+        float jac, wpart, pl, pos;
+        if (ROW) {
+            jac = tt - tx * bt / bx;
+            wpart = (Vz / Vn) * (Vz / Vn);
+            pl = pxl;
+        } else {
+            jac = tt - tz * bt / bz;
+            wpart = (Vx / Vn) * (Vx / Vn);
+            pl = pzl;
+        }
+        pos = (float)((double)i * h) + t * h;
+        float wreal = g.dth * fabsf(jac) * wpart * c_ref * c_ref / (4.f * 3.14159265358979f * sv.v * sv.v);
+        int64_t slot = slot0 + cnt;
+        (ROW ? A.rpos : A.cpos)[slot] = pos;
+        (ROW ? A.rp : A.cp)[slot] = pl;
+        for (int w = 0; w < A.n_omega; ++w) {
+            double om = A.omega_dev[w];
+            float omf = (float)om;
+            float kap = 2.f * sv.Vn / (omf * A.w0 * A.w0);
+            cf dx = {db[0], kap * dT[0]}, dz = {db[1], kap * dT[1]}, dth = {db[2], kap * dT[2]};
+            cf pdd = {pdx * dx.re + pdz * dz.re, pdx * dx.im + pdz * dz.im};
+            cf dpx = {pxl * pdd.re + dpth_x * dth.re, pxl * pdd.im + dpth_x * dth.im};
+            cf dpz = {pzl * pdd.re + dpth_z * dth.re, pzl * pdd.im + dpth_z * dth.im};
+            cf J = {dx.re * Vz - dz.re * Vx, dx.im * Vz - dz.im * Vx};
+            cf M;
+            if (ROW) M = cdiv(cf{dpx.re * Vz - pdx * dz.re, dpx.im * Vz - pdx * dz.im}, J);
+            else M = cdiv(cf{-dpz.re * Vx + pdz * dx.re, -dpz.im * Vx + pdz * dx.im}, J);
+            cf amp = csqrt_pr(cdiv(cf{rho_s * sv.Vn / rho, 0.f}, J));
+            // coef = i * wreal * sigma * amp
+            cf coef = {-wreal * sigma * amp.im, wreal * sigma * amp.re};
+            float ohi = omf, olo = (float)(om - (double)ohi);
+            float ph = phase_mod(ohi, olo, tau_hi, tau_lo, A.C1, A.C2, A.C3);
+            float sp, cp;
+            sincosf(ph, &sp, &cp);
+            cf E = cmul(coef, cf{cp, sp});
+            (ROW ? A.rdat : A.cdat)[(int64_t)w * lines_total + slot] = make_float4(E.re, E.im, M.re, M.im);
+        }
+        ++cnt;
+    }
+    (ROW ? A.rcnt : A.ccnt)[(int64_t)k * nl + line] = cnt;
+}
+
+__global__ void k_sum(SupArgs A, float2 *u) {
+    const Grid2D &g = A.g;
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y;
+    if (ix >= g.nx) return;
+    float xr = (float)((double)ix * g.hx), zr = (float)((double)iz * g.hz);
+    int64_t rows_total = (int64_t)g.nth * g.nz * KC, cols_total = (int64_t)g.nth * g.nx * KC;
+    for (int w = 0; w < A.n_omega; ++w) {
+        float om = (float)A.omega_dev[w];
+        float are = 0.f, aim = 0.f;
+        for (int k = 0; k < g.nth; ++k) {
+            int64_t rl = (int64_t)k * g.nz + iz;
+            int nr = A.rcnt[rl];
+            for (int j = 0; j < nr; ++j) {
+                int64_t s = rl * KC + j;
+                float d = xr - A.rpos[s];
+                float4 q = A.rdat[(int64_t)w * rows_total + s];
+                float ph = om * (A.rp[s] * d + 0.5f * q.z * d * d);
+                float dec = -0.5f * om * q.w * d * d;
+                if (dec < -60.f) continue;
+                float mag = __expf(dec);
+                float sp, cp;
+                sincosf(ph, &sp, &cp);
+                are += mag * (q.x * cp - q.y * sp);
+                aim += mag * (q.x * sp + q.y * cp);
+            }
+            int64_t cl = (int64_t)k * g.nx + ix;
+            int nc = A.ccnt[cl];
+            for (int j = 0; j < nc; ++j) {
+                int64_t s = cl * KC + j;
+                float d = zr - A.cpos[s];
+                float4 q = A.cdat[(int64_t)w * cols_total + s];
+                float ph = om * (A.cp[s] * d + 0.5f * q.z * d * d);
+                float dec = -0.5f * om * q.w * d * d;
+                if (dec < -60.f) continue;
+                float mag = __expf(dec);
+                float sp, cp;
+                sincosf(ph, &sp, &cp);
+                are += mag * (q.x * cp - q.y * sp);
+                aim += mag * (q.x * sp + q.y * cp);
+            }
+        }
+        u[((int64_t)w * g.nz + iz) * g.nx + ix] = make_float2(are, aim);
+    }
+}
+
+constexpr int KMAX_LIMIT = 32;
+
+__global__ void k_arrivals(SupArgs A, uint8_t *count, double *T, float *Aout, int kmax) {
+    const Grid2D &g = A.g;
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y;
+    if (ix >= g.nx) return;
+    float rho_s = A.src[21], c_ref = A.src[22];
+    float rho_r = A.rho[(int64_t)iz * g.nx + ix];
+    int64_t cells = (int64_t)g.nth * g.nx * g.nz;
+    float idth = (float)(1.0 / g.dth);
+    const float pi8 = 25.1327412287183459f;
+    float Tl[KMAX_LIMIT];
+    double Td[KMAX_LIMIT];
+    float Al[KMAX_LIMIT];
+    int n = 0, total = 0;
+    auto B = [&](int k) { return A.B[cidx(g, (k + g.nth) % g.nth, iz, ix)]; };
+    auto acell = [&](int k, float bt) {
+        int64_t o = cidx(g, k, iz, ix);
+        float vr = A.vel[3 * cells + o];
+        return c_ref * c_ref * sqrtf(rho_s / rho_r) / (vr * sqrtf(pi8 * A.VSN[o] * fabsf(bt)));
+    };
+    for (int k = 0; k < g.nth; ++k) {
+        int kn = (k + 1) % g.nth;
+        int64_t o0 = cidx(g, k, iz, ix), o1 = cidx(g, kn, iz, ix);
+        if (!(A.FL[o0] && A.FL[o1])) continue;
+        float b0 = A.B[o0], b1 = A.B[o1];
+        if ((b0 >= 0.f) == (b1 >= 0.f)) continue;
+        ++total;
+        float t = b0 / (b0 - b1);
+        int64_t p0 = pidx(g, k, iz, ix), p1 = pidx(g, kn, iz, ix);
+        float h0 = A.st[3 * g.field + p0], l0 = A.st[4 * g.field + p0];
+        float h1 = A.st[3 * g.field + p1], l1 = A.st[4 * g.field + p1];
+        double Tv = (double)h0 + ((double)l0 + (double)t * ((double)(h1 - h0) + (double)(l1 - l0)));
+        float bt0 = (b1 - B(k - 1)) * 0.5f * idth;
+        float bt1 = (B(k + 2) - b0) * 0.5f * idth;
+        float a0 = acell(k, bt0), a1 = acell(kn, bt1);
+        float Av = a0 + t * (a1 - a0);
+        // insert keeping ascending T (equal T: later angle after)
+        int pos = n;
+        while (pos > 0 && Td[pos - 1] > Tv) --pos;
+        if (pos < kmax) {
+            int last = n < kmax ? n : kmax - 1;
+            for (int j = last; j > pos; --j) { Td[j] = Td[j - 1]; Al[j] = Al[j - 1]; }
+            Td[pos] = Tv;
+            Al[pos] = Av;
+            if (n < kmax) ++n;
+        }
+    }
+    (void)Tl;
+    if (total > kmax) atomicOr(A.err, DeviceErrors::OVERFLOW);
+    int64_t node = (int64_t)iz * g.nx + ix;
+    if (count) count[node] = (uint8_t)n;
+    for (int j = 0; j < kmax; ++j) {
+        if (T) T[node * kmax + j] = j < n ? Td[j] : 0.0;
+        if (Aout) Aout[node * kmax + j] = j < n ? Al[j] : 0.f;
+    }
+}
+
+size_t superpose_scratch_bytes(const Solve &sv) {
+    const Grid2D &g = sv.g;
+    size_t cells = (size_t)g.nth * g.nx * g.nz;
+    size_t rs = (size_t)g.nth * g.nz * KC, cs = (size_t)g.nth * g.nx * KC;
+    size_t no = sv.omega.size();
+    size_t b = cells * (4 + 4 + 1);
+    b = (b + 255) & ~(size_t)255;
+    b += (size_t)g.nth * (g.nz + g.nx) * 4 + 256;
+    b += (rs + cs) * 8 + 512;
+    b += no * (rs + cs) * 16 + 512;
+    b += no * 8 + 256;
+    return b + 4096;  // per-buffer 256-byte alignment slack
+}
+
+static void split_two_pi(float &C1, float &C2, float &C3) {
+    const double two_pi = 6.283185307179586476925286766559;
+    auto trunc_bits = [](double x, int bits) {
+        int e;
+        double m = frexp(x, &e);
+        double sc = ldexp(1.0, bits);
+        return ldexp(floor(m * sc) / sc, e);
+    };
+    double c1 = trunc_bits(two_pi, 15);
+    double c2 = trunc_bits(two_pi - c1, 15);
+    C1 = (float)c1;
+    C2 = (float)c2;
+    C3 = (float)(two_pi - c1 - c2);
+}
+
+cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
+                             float *A_dev, int kmax, unsigned *d_err, cudaStream_t s) {
+    const Grid2D &g = sv.g;
+    size_t cells = (size_t)g.nth * g.nx * g.nz;
+    size_t rs = (size_t)g.nth * g.nz * KC, cs = (size_t)g.nth * g.nx * KC;
+    size_t no = sv.omega.size();
+    char *base = (char *)sv.scratch;
+    auto take = [&](size_t bytes) {
+        char *p = base;
+        base += (bytes + 255) & ~(size_t)255;
+        return (void *)p;
+    };
+    SupArgs A;
+    A.g = g;
+    A.st = sv.state[sv.cur];
+    A.vel = sv.vel;
+    A.rho = sv.m->rho;
+    A.src = sv.src;
+    A.B = (float *)take(cells * 4);
+    A.VSN = (float *)take(cells * 4);
+    A.FL = (uint8_t *)take(cells);
+    A.rcnt = (int *)take((size_t)g.nth * g.nz * 4);
+    A.ccnt = (int *)take((size_t)g.nth * g.nx * 4);
+    A.rpos = (float *)take(rs * 4);
+    A.rp = (float *)take(rs * 4);
+    A.cpos = (float *)take(cs * 4);
+    A.cp = (float *)take(cs * 4);
+    A.rdat = (float4 *)take(no * rs * 16);
+    A.cdat = (float4 *)take(no * cs * 16);
+    double *om = (double *)take(no * 8);
+    if ((size_t)(base - (char *)sv.scratch) > sv.scratch_bytes) return cudaErrorInvalidValue;
+    cudaMemcpyAsync(om, sv.omega.data(), no * 8, cudaMemcpyHostToDevice, s);
+    A.n_omega = (int)no;
+    A.omega_dev = om;
+    A.w0 = (float)sv.w0;
+    A.r0 = (float)sv.r0;
+    double h = g.hx > g.hz ? g.hx : g.hz;
+    double fr = sv.r0 + 2.0 * h;
+    A.flag_r2 = (float)(fr * fr);
+    split_two_pi(A.C1, A.C2, A.C3);
+    A.err = d_err;
+    dim3 gb((g.nx + 127) / 128, g.nz, g.nth);
+    k_beam_fields<<<gb, 128, 0, s>>>(A);
+    if (u_dev) {
+        k_centres<true><<<dim3((g.nz + 63) / 64, g.nth), 64, 0, s>>>(A);
+        k_centres<false><<<dim3((g.nx + 63) / 64, g.nth), 64, 0, s>>>(A);
+        k_sum<<<dim3((g.nx + 127) / 128, g.nz), 128, 0, s>>>(A, u_dev);
+    }
+    if (count_dev || T_dev || A_dev)
+        k_arrivals<<<dim3((g.nx + 63) / 64, g.nz), 64, 0, s>>>(A, count_dev, T_dev, A_dev, kmax);
+    return cudaGetLastError();
+}
+
+}  // namespace egb

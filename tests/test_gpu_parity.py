@@ -1,0 +1,73 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated against the FP64 oracle): traveltime relative <= 1e-5, amplitude relative
+<= 1e-3, complex wavefield relative L2 <= 2e-3, arrival counts bit-exact at every node that is not
+ambiguous (oracle |b| < 1e-4 h at a crossing, where the sign of b is decided below the rounding of
+either side).  The level sets themselves are compared with bounds derived from FP32 rounding over
+the steps taken (labels: 2e-3 h; angle label: 2e-4 rad; tau: relative 1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthmedia
+from tests.gpu_common import compare_outputs, run_gpu, run_oracle, wrap
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {
+        'vti_64': synthmedia.vti_homogeneous(),
+        'vti_ragged': synthmedia.vti_homogeneous(n=45, h=10.0, n_theta=40, steps=60),
+        'tti_96': synthmedia.tti_heterogeneous(n=96, n_theta=64, length=2560.0, steps=260,
+                                                freqs=(10.0, 20.0)),
+    }
+
+
+@pytest.fixture(scope='module', params=list(_cases().keys()))
+def case(request):
+    p = _cases()[request.param]
+    res, info, state, vel = run_gpu(p, read_state=True)
+    ref = run_oracle(p)
+    return request.param, p, res, info, state, vel, ref
+
+
+def test_velocity_parity(case):
+    """Velocities in CFL units (error / spacing / max rate) and v, dp/dt relative to their scale."""
+    name, p, res, info, state, vel, ref = case
+    S = ref['S']
+    rate = S.max_rate
+    for i, key, h in ((0, 'Vx', S.hx), (1, 'Vz', S.hz), (2, 'thetadot', S.dth)):
+        err = np.max(np.abs(vel[i] - S.vel[key])) / h / rate
+        assert err < 1e-6, (name, key, err)
+    err_v = np.max(np.abs(vel[3] - S.vel['v']) / S.vel['v'])
+    assert err_v < 1e-6, (name, 'v', err_v)
+    vmax = np.max(S.vel['v'])
+    for i, key in ((4, 'pdx'), (5, 'pdz')):
+        # an error dp in dp/dt moves dtheta/dt by about v dp: measure it in the same CFL units
+        err = np.max(np.abs(vel[i] - S.vel[key])) * vmax / S.dth / rate
+        assert err < 1e-6, (name, key, err)
+    assert abs(info['dt'] - ref['dt']) / ref['dt'] < 1e-6
+
+
+def test_state_parity(case):
+    name, p, res, info, state, vel, ref = case
+    lab = ref['lab']
+    h = max(p.hx, p.hz)
+    ey = max(np.max(np.abs(state[0] - lab['Yx'])), np.max(np.abs(state[1] - lab['Yz']))) / h
+    et = np.max(np.abs(wrap(state[2] - lab['Th'])))
+    etau = np.max(np.abs(state[3] - lab['tau'])) / np.max(np.abs(lab['tau']))
+    print(name, 'label err/h', ey, 'angle', et, 'tau rel', etau)
+    assert ey < 2e-3 and et < 2e-4 and etau < 1e-6, (name, ey, et, etau)
+
+
+def test_output_parity(case):
+    name, p, res, info, state, vel, ref = case
+    m = compare_outputs(res, ref)
+    print(name, m)
+    assert m['u_rel_l2'] < 2e-3, (name, m)
+    assert m['count_mismatch'] == 0, (name, m)
+    assert m['T_rel_max'] < 1e-5, (name, m)
+    assert m['A_rel_max'] < 1e-3, (name, m)
