@@ -117,6 +117,29 @@ egb_status egb_evolve(egb_ctx *ctx, egb_solve_id solve, int steps, double cfl);
 egb_status egb_superpose(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t *count, double *T,
                          float *A, int kmax);
 
+/* Size of the fixed device scratch used by egb_superpose_noalloc (32 MiB). */
+#define EGB_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* egb_superpose without any device allocation.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory at this point, for example a serving
+ * loop whose device memory is already handed to a pool or caching allocator (a cudaMalloc outside
+ * it can fail or fragment it), or a latency-critical loop that must not hit cudaMalloc/cudaFree
+ * and their implicit device-wide synchronisation.
+ * It computes exactly what egb_superpose computes, but its work buffers live in one statically
+ * sized device array of EGB_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  Restrictions:
+ *   - u_out, count, T, A must be device pointers (or NULL); host pointers give EGB_E_INVALID;
+ *   - a solve whose superposition needs more scratch than EGB_NOALLOC_SCRATCH_BYTES (about
+ *     9 bytes per phase-space cell plus the beam-centre lists, i.e. up to a few million cells) is
+ *     refused with EGB_E_INVALID and a message giving both sizes;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress with
+ *     that device current); make that first call before any stream capture;
+ *   - every call shares the array: calls whose kernels may overlap on the GPU (other streams or
+ *     other contexts on the same device) race and must be serialised by the caller.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+egb_status egb_superpose_noalloc(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t *count,
+                                 double *T, float *A, int kmax);
+
 /* Wait for the context stream and report latched device errors (then clear them). */
 egb_status egb_sync(egb_ctx *ctx);
 

@@ -29,7 +29,7 @@ EGB_FP32_PHASE64, EGB_FP64 = 0, 1
 
 EXPORTED = ('egb_create', 'egb_destroy', 'egb_medium', 'egb_source', 'egb_evolve', 'egb_superpose',
             'egb_sync', 'egb_release', 'egb_last_error', 'egb_get_solve_info', 'egb_read_state',
-            'egb_read_velocity')
+            'egb_read_velocity', 'egb_superpose_noalloc')
 
 
 class EgbError(RuntimeError):
@@ -70,6 +70,7 @@ def load(path: Optional[str] = None):
     lib.egb_source.argtypes = [vp, u64, P(d), i, P(d), d, P(i), d, P(u64)]
     lib.egb_evolve.argtypes = [vp, u64, i, d]
     lib.egb_superpose.argtypes = [vp, u64, vp, vp, vp, vp, i]
+    lib.egb_superpose_noalloc.argtypes = [vp, u64, vp, vp, vp, vp, i]
     lib.egb_sync.argtypes = [vp]
     lib.egb_release.argtypes = [vp, u64]
     lib.egb_last_error.argtypes = [vp]
@@ -146,6 +147,12 @@ def egb_evolve(h, solve, steps, cfl):
 
 def egb_superpose(h, solve, u_out=None, count=None, T=None, A=None, kmax=8):
     _check(h, load().egb_superpose(h, solve, _ptr(u_out), _ptr(count), _ptr(T), _ptr(A), kmax))
+
+
+def egb_superpose_noalloc(h, solve, u_out=None, count=None, T=None, A=None, kmax=8):
+    """egb_superpose into caller-owned DEVICE buffers without any device allocation (the work
+    buffers are a fixed 32 MiB array inside the library); see include/egb.h."""
+    _check(h, load().egb_superpose_noalloc(h, solve, _ptr(u_out), _ptr(count), _ptr(T), _ptr(A), kmax))
 
 
 def egb_sync(h):

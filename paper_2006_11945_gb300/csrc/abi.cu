@@ -339,6 +339,37 @@ egb_status egb_superpose(egb_ctx *c, egb_solve_id sid, void *u_out, uint8_t *cou
     return EGB_OK;
 }
 
+egb_status egb_superpose_noalloc(egb_ctx *c, egb_solve_id sid, void *u_out, uint8_t *count,
+                                 double *T, float *A, int kmax) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    if ((count || T || A) && (kmax < 1 || kmax > 32)) return fail(c, EGB_E_INVALID, "kmax must be in 1..32");
+    DeviceGuard dg(c->device);
+    const void *outs[4] = {u_out, count, T, A};
+    for (const void *p : outs)
+        if (p && !is_device_ptr(p)) return fail(c, EGB_E_INVALID, "egb_superpose_noalloc needs device output pointers");
+    Solve *s = it->second;
+    size_t need = superpose_scratch_bytes(*s);
+    if (need > EGB_NOALLOC_SCRATCH_BYTES)
+        return fail(c, EGB_E_INVALID, "superposition needs %zu bytes of scratch, more than the fixed %u bytes",
+                    need, (unsigned)EGB_NOALLOC_SCRATCH_BYTES);
+    void *fixed = nullptr;
+    cudaError_t e = noalloc_scratch(c->device, &fixed);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fixed scratch lookup");
+    // run the ordinary superposition with the fixed array standing in for the solve's scratch
+    float *own = s->scratch;
+    size_t own_bytes = s->scratch_bytes;
+    s->scratch = (float *)fixed;
+    s->scratch_bytes = EGB_NOALLOC_SCRATCH_BYTES;
+    e = launch_superpose(*s, (float2 *)u_out, count, T, A, kmax, c->d_err, c->stream);
+    s->scratch = own;
+    s->scratch_bytes = own_bytes;
+    if (e != cudaSuccess) return cuda_fail(c, e, "superpose (fixed scratch)");
+    return EGB_OK;
+}
+
 egb_status egb_sync(egb_ctx *c) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);

@@ -127,6 +127,9 @@ cudaError_t launch_rk3_step(Solve &sv, float dt, cudaStream_t s);
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 size_t superpose_scratch_bytes(const Solve &sv);
+// Device address of the fixed superposition scratch (EGB_NOALLOC_SCRATCH_BYTES) on `device`, which
+// must be the current device; looked up once per device.
+cudaError_t noalloc_scratch(int device, void **ptr);
 cudaError_t launch_read_state(const Solve &sv, double *out_dev, cudaStream_t s);
 
 }  // namespace egb

@@ -434,3 +434,33 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
 }
 
 }  // namespace egb
+
+// ---------------------------------------------------------------------------------------------
+// Fixed scratch for egb_superpose_noalloc.  Every GPU that loads the library reserves this array
+// when the module is loaded and keeps it until the process exits.  Host code must not pass the
+// symbol itself to a kernel (in host code it names a host-side stand-in); it asks the runtime for
+// the device address once per device, with that device current, and passes that address.
+// No part of it has to start at zero: each superposition kernel writes every byte it later reads.
+// All calls share it, so two calls whose kernels overlap on the GPU (different streams or
+// contexts on one device) race on it.
+// ---------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EGB_NOALLOC_SCRATCH_BYTES];
+
+namespace egb {
+
+cudaError_t noalloc_scratch(int device, void **ptr) {
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[device] = p;
+    }
+    *ptr = addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace egb
