@@ -45,6 +45,9 @@ def workload(name):
         return synthmedia.tti_heterogeneous(n=512, h=5.0, n_theta=256, freqs=(10.0, 20.0, 40.0))
     if name == 'vti64':
         return synthmedia.vti_homogeneous()
+    if name == 'tti256':
+        return synthmedia.tti_heterogeneous(n=256, n_theta=256, length=2560.0, steps=1400,
+                                            freqs=(10.0, 20.0, 40.0))
     if name == 'tti128':
         return synthmedia.tti_heterogeneous(n=128, n_theta=128, length=2560.0, steps=400,
                                             freqs=(10.0, 20.0, 40.0))
@@ -309,7 +312,7 @@ def main():
     ap.add_argument('--steps', type=int, default=3)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
-    ap.add_argument('--workload', default='tti512', choices=['tti512', 'tti128', 'vti64'])
+    ap.add_argument('--workload', default='tti512', choices=['tti512', 'tti256', 'tti128', 'vti64'])
     ap.add_argument('--evolve-steps', type=int, default=None)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--cpu-seconds', type=float, default=20.0)

@@ -58,6 +58,8 @@ size_t free_bytes() {
 void free_solve(Solve *s) {
     for (auto &p : s->state) cudaFree(p);
     cudaFree(s->vel);
+    cudaFree(s->velp);
+    tma_release(*s);
     cudaFree(s->ball);
     cudaFree(s->src);
     cudaFree(s->scratch);
@@ -224,7 +226,8 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     s->omega.assign(omega, omega + n_omega);
     size_t cells = (size_t)nth * g.nx * g.nz;
     size_t state_b = (size_t)NFIELD * g.field * 4;
-    s->bytes = 3 * state_b + cells * 6 * 4 + g.nz * 8 + (24 + 4 * nth) * 4;
+    size_t velp_b = (size_t)3 * g.field * 4;
+    s->bytes = 3 * state_b + cells * 6 * 4 + velp_b + g.nz * 8 + (24 + 4 * nth) * 4;
     if (s->bytes + (256u << 20) > free_bytes()) {
         delete s;
         return fail(c, EGB_E_NOMEM, "solve needs %zu bytes of device memory", (size_t)(s->bytes));
@@ -233,9 +236,13 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     for (auto &p : s->state)
         if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
     if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 6 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->velp, velp_b);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->velp, 0, velp_b, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&s->ball, g.nz * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_solve(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
+    e = tma_prepare(*s);
+    if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "tensor maps of the stencil"); }
     // frozen source ball: per row the ix range with (x - xs)^2 + (z - zs)^2 <= r0^2 (FP64)
     std::vector<int2> ball(g.nz);
     for (int iz = 0; iz < g.nz; ++iz) {
@@ -283,7 +290,7 @@ egb_status egb_evolve(egb_ctx *c, egb_solve_id sid, int steps, double cfl) {
     DeviceGuard dg(c->device);
     s->dt = cfl / s->max_rate;
     for (int i = 0; i < steps; ++i) {
-        cudaError_t e = launch_rk3_step(*s, (float)s->dt, c->stream);
+        cudaError_t e = launch_rk3_step_tma(*s, (float)s->dt, c->d_err, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "evolve launch");
     }
     s->steps += steps;

@@ -97,6 +97,8 @@ struct Solve {
     float *state[3] = {nullptr, nullptr, nullptr};  // three padded buffers of NFIELD fields
     int cur = 0;                                     // buffer holding u^n
     float *vel = nullptr;   // [6][nth][nz][nx]: Vx, Vz, thetadot, v, pdx, pdz
+    float *velp = nullptr;  // [3][nth][nz+4][pitch]: Vx, Vz, thetadot in the padded state layout
+    void *tma = nullptr;    // tensor maps of the TMA stencil
     int2 *ball = nullptr;   // [nz] frozen ix range per row (lo > hi: none)
     float *src = nullptr;   // source block: a_s[21], rho_s, c_ref, then [nth] x (psx, psz)
     float *scratch = nullptr;  // superposition scratch (lazily sized)
@@ -124,6 +126,9 @@ cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const floa
 cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, cudaStream_t s);
 cudaError_t launch_init_state(const Solve &sv, cudaStream_t s);
 cudaError_t launch_rk3_step(Solve &sv, float dt, cudaStream_t s);
+cudaError_t tma_prepare(Solve &sv);
+void tma_release(Solve &sv);
+cudaError_t launch_rk3_step_tma(Solve &sv, float dt, unsigned *d_err, cudaStream_t s);
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 size_t superpose_scratch_bytes(const Solve &sv);

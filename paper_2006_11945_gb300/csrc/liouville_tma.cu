@@ -1,0 +1,428 @@
+// TMA-staged Liouville stencil (the hot loop): persistent, streaming along theta.
+//
+// Same scheme as the plain stage kernel (Eqs. 16, 19 in pseudo-time; third-order HJ-WENO upwinded
+// by the velocity sign; Shu-Osher TVD-RK3 in increment form; double-float tau; wrapped angle-label
+// differences; frozen ball copies u^n), organised for GB300:
+//
+//  * one CTA per SM loops over work items (x-tile of 64 cells, z-tile of 8 rows, theta chunk);
+//  * for each theta plane a single 4-D TMA copy brings all five state fields of the tile plus its
+//    x/z halo (a 72 x 12 box: x from -4 so the copy starts on a 16-byte boundary, z from -2) into a
+//    ring of shared-memory slots; the theta stencil reads the neighbouring planes' slots, so every
+//    plane is fetched from HBM once per tile and chunk;
+//  * u^n (stages 2, 3) and the stored velocities of the centre plane come by a second TMA copy;
+//  * mbarrier transaction counts track completion; every wait is bounded and a timeout latches
+//    EGB_E_TIMEOUT, drains the copies in flight and leaves the kernel;
+//  * each thread updates two neighbouring x cells with packed FP32x2 arithmetic where it maps.
+#include <cuda.h>
+
+#include "egb_internal.cuh"
+
+namespace egb {
+
+namespace tma {
+constexpr int TX = 64, TZ = 8;                     // tile (cells)
+constexpr int HX = TX + 8, HZ = TZ + 4;            // halo box (x -4..67, z -2..9)
+constexpr int RING = 7, RING2 = 3;                 // plane slots, centre-plane slots
+constexpr int HALO_FLOATS = NFIELD * HZ * HX;      // 4320
+constexpr int UN_FLOATS = NFIELD * TZ * TX;        // 2560
+constexpr int V_FLOATS = 3 * TZ * TX;              // 1536
+constexpr int SLOT2_FLOATS = UN_FLOATS + V_FLOATS;
+constexpr size_t SMEM_BYTES = sizeof(float) * ((size_t)RING * HALO_FLOATS + (size_t)RING2 * SLOT2_FLOATS) +
+                              8 * (RING + RING2);
+constexpr int THREADS = 256;
+}  // namespace tma
+
+struct TmaArgs {
+    Grid2D g;
+    float *out;
+    const int2 *ball;
+    float dt, coef, ihx, ihz, idth;
+    float eps[4];
+    int tiles_x, tiles_z, chunk, nchunks, items;
+    unsigned *err;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (seconds), returning false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        if (mbar_try_wait(b, parity)) return true;
+        if (i > 16) __nanosleep(128);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            int c3, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4, %5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- packed two-cell arithmetic ------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ float2 wrap2(float2 d) {
+    const float two_pi = 6.28318530717958647692f;
+    const float inv = 0.159154943091895335769f;
+    float2 k = f2(rintf(d.x * inv), rintf(d.y * inv));
+    return fma2(f2(-two_pi, -two_pi), k, d);
+}
+
+// Third-order HJ-WENO for two cells (see the plain kernel for the formula).
+__device__ __forceinline__ float2 weno3_2(const float2 d[4], float2 vel, float eps) {
+    bool lx = vel.x > 0.f, ly = vel.y > 0.f;
+    float2 P = f2(lx ? d[0].x : d[3].x, ly ? d[0].y : d[3].y);
+    float2 Q = f2(lx ? d[1].x : d[2].x, ly ? d[1].y : d[2].y);
+    float2 R = f2(lx ? d[2].x : d[1].x, ly ? d[2].y : d[1].y);
+    float2 qp = sub2(Q, P), rq = sub2(R, Q);
+    float2 e2 = f2(eps, eps);
+    float2 A = fma2(qp, qp, e2);
+    float2 B = fma2(rq, rq, e2);
+    float2 B2 = mul2(B, B);
+    float2 den = fma2(mul2(A, A), f2(2.f, 2.f), B2);
+    float2 w = f2(__fdividef(B2.x, den.x), __fdividef(B2.y, den.y));
+    float2 centre = mul2(add2(d[1], d[2]), f2(0.5f, 0.5f));
+    float2 curv = add2(sub2(P, add2(Q, Q)), R);
+    return fma2(mul2(w, f2(-0.5f, -0.5f)), curv, centre);
+}
+
+__device__ __forceinline__ float2 deriv2(const float2 s[5], float2 vel, float eps, bool angle) {
+    float2 d[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        d[j] = sub2(s[j + 1], s[j]);
+        if (angle) d[j] = wrap2(d[j]);
+    }
+    return weno3_2(d, vel, eps);
+}
+
+__device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5], float2 vel, float eps) {
+    float2 d[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] = add2(sub2(h[j + 1], h[j]), sub2(l[j + 1], l[j]));
+    return weno3_2(d, vel, eps);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(tma::THREADS, 1)
+    k_rk3_tma(const __grid_constant__ CUtensorMap mapK, const __grid_constant__ CUtensorMap mapN,
+              const __grid_constant__ CUtensorMap mapV, TmaArgs A) {
+    using namespace tma;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring = reinterpret_cast<float *>(smem);
+    float *ring2 = ring + RING * HALO_FLOATS;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ring2 + RING2 * SLOT2_FLOATS);
+    uint64_t *bar2 = bar + RING;
+    __shared__ int abort_flag;
+    const Grid2D &g = A.g;
+    const int tid = threadIdx.x;
+    const int tx = tid & 31, tz = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < RING + RING2; ++s) mbar_init(bar + s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+    uint32_t phase = 0, phase2 = 0;      // parity bit per slot (identical in every thread)
+    uint32_t pending = 0, pending2 = 0;  // slots with a copy in flight (thread 0 only)
+    const uint32_t bytes_halo = HALO_FLOATS * 4;
+    const uint32_t bytes2 = (STAGE == 1 ? V_FLOATS : SLOT2_FLOATS) * 4;
+    const int64_t F = g.field;
+
+    for (int item = blockIdx.x; item < A.items; item += gridDim.x) {
+        int xt = item % A.tiles_x;
+        int rest = item / A.tiles_x;
+        int zt = rest % A.tiles_z;
+        int ch = rest / A.tiles_z;
+        int k0 = ch * A.chunk;
+        int kn = min(A.chunk, g.nth - k0);
+        int x0 = xt * TX, z0 = zt * TZ;
+        int nplanes = kn + 4;
+        auto plane_of = [&](int j) { return (k0 - 2 + j + 2 * g.nth) % g.nth; };
+        auto issue = [&](int j) {
+            int s = j % RING;
+            mbar_expect_tx(bar + s, bytes_halo);
+            tma_load_4d(ring + s * HALO_FLOATS, &mapK, x0, z0, plane_of(j), 0, bar + s);
+            pending |= 1u << s;
+        };
+        auto issue2 = [&](int j) {
+            int s = j % RING2;
+            mbar_expect_tx(bar2 + s, bytes2);
+            float *dst = ring2 + s * SLOT2_FLOATS;
+            int k = k0 + j;
+            if (STAGE != 1) tma_load_4d(dst, &mapN, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
+            tma_load_4d(dst + UN_FLOATS, &mapV, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
+            pending2 |= 1u << s;
+        };
+        if (tid == 0) {
+            for (int j = 0; j < min(RING, nplanes); ++j) issue(j);
+            for (int j = 0; j < min(RING2, kn); ++j) issue2(j);
+        }
+        bool ok = true;
+        for (int j = 0; j < 4 && ok; ++j) {
+            int s = j % RING;
+            ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u);
+            phase ^= 1u << s;
+            if (tid == 0) pending &= ~(1u << s);
+        }
+        const int iz = z0 + tz;
+        const int ixa = x0 + 2 * tx;
+        const bool row_ok = iz < g.nz;
+        const int2 br = row_ok ? A.ball[iz] : make_int2(1, 0);
+        for (int kk = 0; kk < kn; ++kk) {
+            {
+                int s = (kk + 4) % RING;
+                if (ok) ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u);
+                phase ^= 1u << s;
+                if (tid == 0) pending &= ~(1u << s);
+                int s2 = kk % RING2;
+                if (ok) ok = mbar_wait_bounded(bar2 + s2, (phase2 >> s2) & 1u);
+                phase2 ^= 1u << s2;
+                if (tid == 0) pending2 &= ~(1u << s2);
+            }
+            if (!ok) atomicOr(&abort_flag, 1);
+            const int k = k0 + kk;
+            const float *slot[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) slot[m] = ring + ((kk + m) % RING) * HALO_FLOATS;
+            const float *s2 = ring2 + (kk % RING2) * SLOT2_FLOATS;
+            if (ok && row_ok && ixa < g.nx) {
+                const int ci = (tz + 2) * HX + 2 * tx + 4;   // centre (first cell) in a halo slot
+                const int cn = tz * TX + 2 * tx;             // centre in an interior slot
+                const float2 vx = *reinterpret_cast<const float2 *>(s2 + UN_FLOATS + cn);
+                const float2 vz = *reinterpret_cast<const float2 *>(s2 + UN_FLOATS + TZ * TX + cn);
+                const float2 vt = *reinterpret_cast<const float2 *>(s2 + UN_FLOATS + 2 * TZ * TX + cn);
+                float2 L[4];
+                float2 ukc[NFIELD];
+                auto gather = [&](int f, float2 sx[5], float2 sz[5], float2 st[5]) {
+                    const float *c = slot[2] + f * HZ * HX + ci;
+                    float2 a = *reinterpret_cast<const float2 *>(c - 2);
+                    float2 b = *reinterpret_cast<const float2 *>(c);
+                    float2 e = *reinterpret_cast<const float2 *>(c + 2);
+                    sx[0] = a; sx[1] = f2(a.y, b.x); sx[2] = b; sx[3] = f2(b.y, e.x); sx[4] = e;
+#pragma unroll
+                    for (int m = 0; m < 5; ++m)
+                        sz[m] = *reinterpret_cast<const float2 *>(c + (m - 2) * HX);
+#pragma unroll
+                    for (int m = 0; m < 5; ++m)
+                        st[m] = *reinterpret_cast<const float2 *>(slot[m] + f * HZ * HX + ci);
+                };
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    float2 sx[5], sz[5], st[5];
+                    gather(f, sx, sz, st);
+                    ukc[f] = sx[2];
+                    // the angle label is continuous in x and z (no 2 pi seam inside a plane), so only
+                    // its theta differences need wrapping
+                    bool ang = (f == 2);
+                    float2 ux = deriv2(sx, vx, A.eps[f], false);
+                    float2 uz = deriv2(sz, vz, A.eps[f], false);
+                    float2 ut = deriv2(st, vt, A.eps[f], ang);
+                    float2 acc = mul2(mul2(vx, ux), f2(A.ihx, A.ihx));
+                    acc = fma2(mul2(vz, uz), f2(A.ihz, A.ihz), acc);
+                    acc = fma2(mul2(vt, ut), f2(A.idth, A.idth), acc);
+                    L[f] = f2(-acc.x, -acc.y);
+                }
+                {
+                    float2 hx5[5], hz5[5], ht5[5], lx5[5], lz5[5], lt5[5];
+                    gather(3, hx5, hz5, ht5);
+                    gather(4, lx5, lz5, lt5);
+                    ukc[3] = hx5[2];
+                    ukc[4] = lx5[2];
+                    float2 ux = deriv2_ff(hx5, lx5, vx, A.eps[3]);
+                    float2 uz = deriv2_ff(hz5, lz5, vz, A.eps[3]);
+                    float2 ut = deriv2_ff(ht5, lt5, vt, A.eps[3]);
+                    float2 acc = mul2(mul2(vx, ux), f2(A.ihx, A.ihx));
+                    acc = fma2(mul2(vz, uz), f2(A.ihz, A.ihz), acc);
+                    acc = fma2(mul2(vt, ut), f2(A.idth, A.idth), acc);
+                    L[3] = sub2(f2(1.f, 1.f), acc);
+                }
+                float2 un[NFIELD];
+#pragma unroll
+                for (int f = 0; f < NFIELD; ++f)
+                    un[f] = (STAGE == 1) ? ukc[f] : *reinterpret_cast<const float2 *>(s2 + f * TZ * TX + cn);
+                const float2 dt2 = f2(A.dt, A.dt), cf2 = f2(A.coef, A.coef);
+                float2 o[NFIELD];
+#pragma unroll
+                for (int f = 0; f < 3; ++f)
+                    o[f] = fma2(cf2, fma2(dt2, L[f], sub2(ukc[f], un[f])), un[f]);
+                {
+                    float2 inc = mul2(cf2, fma2(dt2, L[3], add2(sub2(ukc[3], un[3]), sub2(ukc[4], un[4]))));
+                    ff ra = ff_add_f(un[3].x, un[4].x, inc.x);
+                    ff rb = ff_add_f(un[3].y, un[4].y, inc.y);
+                    o[3] = f2(ra.hi, rb.hi);
+                    o[4] = f2(ra.lo, rb.lo);
+                }
+                const bool fa = ixa >= br.x && ixa <= br.y;
+                const bool fb = ixa + 1 >= br.x && ixa + 1 <= br.y;
+                const int64_t p = pidx(g, k, iz, ixa);
+#pragma unroll
+                for (int f = 0; f < NFIELD; ++f) {
+                    float2 v = f2(fa ? un[f].x : o[f].x, fb ? un[f].y : o[f].y);
+                    if (ixa + 1 < g.nx) *reinterpret_cast<float2 *>(A.out + f * F + p) = v;
+                    else A.out[f * F + p] = v.x;
+                }
+            }
+            __syncthreads();
+            if (abort_flag) break;
+            if (tid == 0) {
+                if (kk + RING < nplanes) issue(kk + RING);
+                if (kk + RING2 < kn) issue2(kk + RING2);
+            }
+        }
+        if (abort_flag) break;
+    }
+    if (abort_flag) {
+        // latch the timeout and drain the copies this CTA still has in flight (bounded)
+        if (tid == 0) {
+            atomicOr(A.err, DeviceErrors::TIMEOUT);
+            for (int s = 0; s < RING; ++s)
+                if (pending & (1u << s)) mbar_wait_bounded(bar + s, (phase >> s) & 1u);
+            for (int s = 0; s < RING2; ++s)
+                if (pending2 & (1u << s)) mbar_wait_bounded(bar2 + s, (phase2 >> s) & 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- host side -----------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 4-D map over a padded field stack: dims {pitch, nz + 4, nth, nfields}, box {bx, bz, 1, nfields}.
+static cudaError_t make_map(CUtensorMap *m, const Grid2D &g, float *base, int nfields, int bx, int bz) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.nz + 2 * ZPAD), (cuuint64_t)g.nth,
+                          (cuuint64_t)nfields};
+    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.field * 4};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)bz, 1, (cuuint32_t)nfields};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+struct TmaMaps {
+    CUtensorMap halo[3], inner[3], vel;
+};
+
+cudaError_t tma_prepare(Solve &sv) {
+    TmaMaps *m = new TmaMaps();
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
+        e = make_map(&m->halo[b], sv.g, sv.state[b], NFIELD, tma::HX, tma::HZ);
+        if (e == cudaSuccess) e = make_map(&m->inner[b], sv.g, sv.state[b], NFIELD, tma::TX, tma::TZ);
+    }
+    if (e == cudaSuccess) e = make_map(&m->vel, sv.g, sv.velp, 3, tma::TX, tma::TZ);
+    if (e != cudaSuccess) {
+        delete m;
+        return e;
+    }
+    sv.tma = m;
+    static bool attr_done = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_rk3_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        attr_done = true;
+    }
+    return cudaGetLastError();
+}
+
+void tma_release(Solve &sv) {
+    delete (TmaMaps *)sv.tma;
+    sv.tma = nullptr;
+}
+
+cudaError_t launch_rk3_step_tma(Solve &sv, float dt, unsigned *d_err, cudaStream_t s) {
+    const Grid2D &g = sv.g;
+    TmaMaps *maps = (TmaMaps *)sv.tma;
+    TmaArgs A;
+    A.g = g;
+    A.ball = sv.ball;
+    A.dt = dt;
+    A.ihx = (float)(1.0 / g.hx);
+    A.ihz = (float)(1.0 / g.hz);
+    A.idth = (float)(1.0 / g.dth);
+    double h = g.hx > g.hz ? g.hx : g.hz;
+    A.eps[0] = A.eps[1] = (float)(1e-6 * h * h);
+    A.eps[2] = (float)(1e-6 * g.dth * g.dth);
+    A.eps[3] = (float)(1e-6 * (h / sv.c_ref) * (h / sv.c_ref));
+    A.tiles_x = (g.nx + tma::TX - 1) / tma::TX;
+    A.tiles_z = (g.nz + tma::TZ - 1) / tma::TZ;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long tiles = (long)A.tiles_x * A.tiles_z;
+    long want = (long)g.nth * tiles / (4L * sms);
+    int chunk = (int)(want < 8 ? 8 : (want > 64 ? 64 : want));
+    if (chunk > g.nth) chunk = g.nth;
+    A.chunk = chunk;
+    A.nchunks = (g.nth + chunk - 1) / chunk;
+    A.items = (int)(tiles * A.nchunks);
+    A.err = d_err;
+    int grid = A.items < sms ? A.items : sms;
+    int n = sv.cur, b1 = (sv.cur + 1) % 3, b2 = (sv.cur + 2) % 3;
+    // stage 1: u1 = u + dt L(u)
+    A.out = sv.state[b1];
+    A.coef = 1.f;
+    k_rk3_tma<1><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(maps->halo[n], maps->inner[n], maps->vel, A);
+    // stage 2: u2 = u + 1/4 ((u1 - u) + dt L(u1))
+    A.out = sv.state[b2];
+    A.coef = 0.25f;
+    k_rk3_tma<2><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(maps->halo[b1], maps->inner[n], maps->vel, A);
+    // stage 3: u_new = u + 2/3 ((u2 - u) + dt L(u2))
+    A.out = sv.state[b1];
+    A.coef = 2.f / 3.f;
+    k_rk3_tma<3><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(maps->halo[b2], maps->inner[n], maps->vel, A);
+    sv.cur = b1;
+    return cudaGetLastError();
+}
+
+}  // namespace egb

@@ -132,7 +132,7 @@ __global__ void k_source(Medium m, double xs, double zs, int nth, float *src) {
 
 // ------------------------------- velocities ------------------------------------------------------
 __global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, float *__restrict__ vel,
-                           float *rate_out) {
+                           float *__restrict__ velp, float *rate_out) {
     int node = blockIdx.x * blockDim.x + threadIdx.x;
     int nodes = g.nx * g.nz;
     float rmax = 0.f;
@@ -156,6 +156,10 @@ __global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, fl
             vel[3 * cells + o] = r.v;
             vel[4 * cells + o] = r.pdx;
             vel[5 * cells + o] = r.pdz;
+            int64_t pp = pidx(g, k, node / g.nx, node % g.nx);
+            velp[pp] = r.Vx;
+            velp[g.field + pp] = r.Vz;
+            velp[2 * g.field + pp] = r.td;
             rmax = fmaxf(rmax, fabsf(r.Vx) * ihx + fabsf(r.Vz) * ihz + fabsf(r.td) * idth);
         }
     }
@@ -175,7 +179,7 @@ cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, 
     (void)d_err;
     k_source<<<(sv.g.nth + 127) / 128, 128, 0, s>>>(*sv.m, sv.xs, sv.zs, sv.g.nth, sv.src);
     int nodes = sv.g.nx * sv.g.nz;
-    k_velocity<<<(nodes + 127) / 128, 128, 0, s>>>(*sv.m, sv.g, sv.src, sv.vel, d_rate);
+    k_velocity<<<(nodes + 127) / 128, 128, 0, s>>>(*sv.m, sv.g, sv.src, sv.vel, sv.velp, d_rate);
     return cudaGetLastError();
 }
 

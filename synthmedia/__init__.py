@@ -244,9 +244,9 @@ def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 
 def tti_default_steps(n, h):
     """Pseudo-time steps for the TTI medium: 1.1 x (latest exit time of source rays) / dt.
 
-    The exit time (0.95 s for the 2560 m square) and the CFL-0.5 time step (which scales with h)
-    were measured for this medium family; the count is fixed here so that every run of the
-    workload advances the same number of steps.
+    Estimates for this medium family on the 2560 m square: latest exit time 0.95 s and a CFL-0.5
+    time step of 0.5 h / 6700 m/s; the count is fixed here so that every run of the workload
+    advances the same number of steps (2801 at 512 x 512, 5 m).
     """
     t_exit = 0.95 * (n * h) / 2560.0
     dt = 0.5 * h / 6700.0  # CFL-0.5 step bound: max(|Vx| + |Vz|) <= 6700 m/s in this family
