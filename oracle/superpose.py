@@ -7,31 +7,31 @@ dynamic ray tracing of Eq. 21 with the complex initial data of Eq. 24), amplitud
 
 Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only):
 
-* Beams are centred at every receiver phase cell (x0, theta) and evaluated at the source; by the
-  reciprocity of the elastic Green's function this sums the same beams, and every beam centre is a
-  grid cell (the paper's advantage (2): no interpolation).  The ray through (x0, theta) carries the
-  level-set labels (Y, vartheta, tau); its impact parameter at the source is
+* The ray through a phase cell (x, theta) carries the level-set labels (Y, vartheta, tau); its
+  impact parameter at the source is
       b = (Y - x_s) x g_s(vartheta)          (2-D cross product a x b = a_x b_z - a_z b_x)
   with g_s the unit group direction of the source medium, so Gamma = {b = 0} (Eq. 35).
-* Dynamic ray tracing from the level sets: a phase-space perturbation (dx, dz, dtheta) at the cell
-  moves the source-end invariants by (db, dvartheta) = grad(b, vartheta) . (dx, dz, dtheta), with
-  the gradients taken by centred differences of the labels.  The beam launched from x0 has the
-  complex initial perturbation dx = n_theta (unit wavefront tangent), dtheta = kappa with
-  kappa = -2 i v(x0, theta) / (omega w0^2), so its wavefront Hessian has imaginary part 2/(omega w0^2)
-  (|beam| falls to 1/e at w0: the beam-width parameter of Eq. 24).
-* At the source (a homogeneous ball) the reversed beam's transverse Hessian is
-      m = -(|V_s| / v_s^2) dvartheta / db
-  and its phase there is exactly tau(x0, theta) + m b^2 / 2 (the linear term of Eq. 25 vanishes
-  because tau carries the plane-wave time p_s . (Y - x_s) at the ball).
-* Amplitude (Eq. 26 with the elastic transport div(rho U^2 V) = 0):
-      sqrt(rho_r v_r / (rho_s |V_s| db)) on the principal branch, times -1 where d_theta b > 0 (one
-      caustic passed: the middle branch of a triplication; KMAH index 1).
-* Weight (the calibrated Psi_0 of Eqs. 30-33): i c_ref^2 / (4 pi v_r^2 rho_r) dtheta, output scaled
-  by rho_s c_ref^2 with c_ref the source phase velocity along +z, so that a homogeneous isotropic
-  medium gives the 2-D Helmholtz Green's function (i/4) H0^(1)(kr) as kr -> inf.  Phase convention
-  exp(+i omega T) from Eq. 2.
-* Only rays that left the source ball count: a cell is taken with weight taper(|Y - x_s|) = 1 below
-  r0 + h, 0 above r0 + 3h, raised cosine between.
+* Beam centres: for every theta and every grid row, each sign change of b between neighbouring
+  ball-origin cells is one point of Gamma; everything there is interpolated linearly.  The beam is
+  evaluated at the receivers of the same row with the horizontal offset (the paper's same-depth
+  evaluation); flat rays are served the same way along grid columns, and the two are blended by
+  the partition of unity g_z^2 + g_x^2 = 1 of the beam's unit group direction.
+* Dynamic ray tracing from the level sets (in place of advecting Eq. 21): with k1 = grad b,
+  k2 = grad vartheta (centred differences in x, z, theta) and e_t = (Vx, Vz, thetadot), the
+  phase-space perturbation with (db, dvartheta) = (1, kappa) is
+      d = (k2 x e_t + kappa e_t x k1) / (e_t . (k1 x k2));
+  kappa = 2 i |V_s| / (omega w0^2) gives the beam a wavefront Hessian i 2/(omega w0^2) at the source
+  (|beam| = 1/e at w0; the complex initial data of Eq. 24).  With dx = (d_x, d_z) and
+  dp = p (pdot . dx) + dp/dtheta d_theta, M [dx, V] = [dp, pdot] gives the Cartesian Hessian
+  (Eq. 25's M = B C^-1) and J = dx x V the complex spreading (det C of Eq. 26).
+* Amplitude (Eq. 26 with the elastic transport div(rho U^2 V) = 0): sigma sqrt(rho_s |V_s| / (rho J))
+  on the principal branch, sigma = -1 where the take-off part of J is negative (KMAH index 1).
+* Weight (the calibrated Psi_0 of Eqs. 30-33): i c_ref^2 / (4 pi v_s(vartheta)^2) times the
+  take-off measure |d vartheta_c / d theta| dtheta, so that a homogeneous isotropic medium gives
+  the 2-D Helmholtz Green's function (i/4) H0^(1)(kr) as kr -> inf; the output is rho_s c_ref^2
+  times the scalar qP Green's function (c_ref: source phase velocity along +z), phase exp(+i omega T)
+  (Eq. 2).
+* Only rays that left the source ball count: a cell is ball-origin when |Y - x_s| <= r0 + 2h.
 
 Arrivals (late arrivals included, Eq. 35): along theta at a node, every sign change of b between
 cells k and k+1 (sign(0) = +1) where both cells have |Y - x_s| <= r0 + 2h; T is tau interpolated
