@@ -225,6 +225,7 @@ def run_egb(args):
         'config': {'workload': f'{p.name} {p.nx}x{p.nz} at {p.hx:g} m x {p.n_theta} angles, '
                                f'{steps_evolve} TVD-RK3 steps, {len(p.freqs)} frequencies',
                    'cells': cells, 'evolve_steps': steps_evolve, 'freqs_hz': p.freqs,
+                   'tile_chunk': info.get('tile_chunk'),
                    'parallelism': f'replicas x{ws}', 'l2': 'state (1.3 GB) larger than L2, no flush'},
         'solves_per_s': ws * args.steps / (ms / 1e3),
         'beam_point_sums_per_s': ws * args.steps * p.nx * p.nz * p.n_theta * len(p.freqs) / (ms / 1e3),
@@ -236,6 +237,9 @@ def run_egb(args):
         'gpu_launches': launches * args.steps,
         'clocks': clk.summary(),
     }
+    if not args.no_fp64_form:
+        line['fp64_form'] = fp64_form(p, args.fp64_steps, local)
+        line['fp64_form']['speedup'] = line['value'] / ws / line['fp64_form']['value']
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line['cpu_baseline'] = cpu_baseline(p, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -243,6 +247,37 @@ def run_egb(args):
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def fp64_form(p, steps, device):
+    """The plain all-FP64 GPU form on the same workload, evolution timed over `steps` steps.
+
+    Returns its cell-update rate and the solves/s it implies for the workload's full step count
+    (setup and superposition excluded, which favours the FP64 form)."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    stream = torch.cuda.Stream()
+    ctx = egb.Context(device, stream.cuda_stream, precision=egb.EGB_FP64)
+    m = ctx.medium_2d(p)
+    s = ctx.source_2d(m, p)
+    egb.egb_evolve(ctx.h, s, 1, p.cfl)
+    egb.egb_sync(ctx.h)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+    egb.egb_evolve(ctx.h, s, steps, p.cfl)
+    with torch.cuda.stream(stream):
+        t1.record(stream)
+    egb.egb_sync(ctx.h)
+    ms = t0.elapsed_time(t1)
+    egb.egb_release(ctx.h, s)
+    egb.egb_release(ctx.h, m)
+    ctx.close()
+    rate = p.cells * steps / (ms / 1e3)
+    return {'value': rate, 'unit': 'cell-updates/s', 'timed_steps': steps,
+            'solves_per_s': rate / (p.cells * p.steps),
+            'note': 'plain FP64 stencil, one thread per cell, evolution only'}
 
 
 def _oracle_sample(p, sub=128):
@@ -316,6 +351,8 @@ def main():
     ap.add_argument('--evolve-steps', type=int, default=None)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--cpu-seconds', type=float, default=20.0)
+    ap.add_argument('--no-fp64-form', action='store_true')
+    ap.add_argument('--fp64-steps', type=int, default=20)
     args = ap.parse_args()
     if args.impl == 'reference':
         run_reference(args)

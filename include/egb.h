@@ -104,6 +104,14 @@ egb_status egb_source(egb_ctx *ctx, egb_medium_id medium, const double xs[3], in
  * twice with s1 and s2 equals one call with s1 + s2.  Asynchronous.  Errors: EGB_E_INVALID. */
 egb_status egb_evolve(egb_ctx *ctx, egb_solve_id solve, int steps, double cfl);
 
+/* Advance several solves of this context together: solve i by steps[i] TVD-RK3 steps at Courant
+ * number cfl (same scheme as egb_evolve, results bit-identical to advancing each alone).  Each RK
+ * stage is one persistent launch over the tiles of every solve still advancing; whole 3-step
+ * rotations are captured into a CUDA graph and replayed.  Solves must use EGB_FP32_PHASE64 and be
+ * distinct.  Asynchronous.  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_CUDA. */
+egb_status egb_evolve_batch(egb_ctx *ctx, int n, const egb_solve_id *solves, const int *steps,
+                            double cfl);
+
 /* Superpose the Gaussian beams (Eqs. 25-26, 33-35) and extract arrivals.
  *   u_out   complex64 [n_omega][nz][nx] (interleaved re, im), or NULL
  *   count   uint8 [nz][nx] number of arrivals kept per node, or NULL
@@ -158,6 +166,7 @@ typedef struct {
     double c_ref;          /* source qP phase velocity along +z (m/s) */
     uint64_t cells;        /* nx * nz * n_theta */
     uint64_t device_bytes; /* device memory held by the solve */
+    int tile_chunk;        /* theta planes per stencil work item chosen by the autotuner (0: FP64) */
 } egb_solve_info;
 
 egb_status egb_get_solve_info(egb_ctx *ctx, egb_solve_id solve, egb_solve_info *out);

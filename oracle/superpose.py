@@ -15,7 +15,8 @@ Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only)
   ball-origin cells is one point of Gamma; everything there is interpolated linearly.  The beam is
   evaluated at the receivers of the same row with the horizontal offset (the paper's same-depth
   evaluation); flat rays are served the same way along grid columns, and the two are blended by
-  the partition of unity g_z^2 + g_x^2 = 1 of the beam's unit group direction.
+  the partition of unity b_x^2/|grad b|^2 + b_z^2/|grad b|^2 = 1 of the level line of b (in a
+  homogeneous medium grad b is normal to the ray, so this is g_z^2 + g_x^2 of the group direction).
 * Dynamic ray tracing from the level sets (in place of advecting Eq. 21): with k1 = grad b,
   k2 = grad vartheta (centred differences in x, z, theta) and e_t = (Vx, Vz, thetadot), the
   phase-space perturbation with (db, dvartheta) = (1, kappa) is
@@ -25,7 +26,8 @@ Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only)
   dp = p (pdot . dx) + dp/dtheta d_theta, M [dx, V] = [dp, pdot] gives the Cartesian Hessian
   (Eq. 25's M = B C^-1) and J = dx x V the complex spreading (det C of Eq. 26).
 * Amplitude (Eq. 26 with the elastic transport div(rho U^2 V) = 0): sigma sqrt(rho_s |V_s| / (rho J))
-  on the principal branch, sigma = -1 where the take-off part of J is negative (KMAH index 1).
+  on the principal branch, sigma = -1 where arg J < -1e-3 (J has crossed the negative real axis at a
+  caustic: KMAH index 1; near the source J is close to the positive real axis and sigma = +1).
 * Weight (the calibrated Psi_0 of Eqs. 30-33): i c_ref^2 / (4 pi v_s(vartheta)^2) times the
   take-off measure |d vartheta_c / d theta| dtheta, so that a homogeneous isotropic medium gives
   the 2-D Helmholtz Green's function (i/4) H0^(1)(kr) as kr -> inf; the output is rho_s c_ref^2
@@ -46,6 +48,9 @@ import math
 import numpy as np
 
 from . import christoffel as _ch
+
+
+KMAH_ARG = 1e-3
 
 
 def _wrap(d):
@@ -167,18 +172,30 @@ def beam_centres(S, lab, F, axis, omega, beam_width):
     J_theta = d_T[:, 0] * V[:, 1] - d_T[:, 1] * V[:, 0]
     Mxx = (dp[:, 0] * V[:, 1] - pdot[:, 0] * dx[:, 1]) / J
     Mzz = (-dp[:, 1] * V[:, 0] + pdot[:, 1] * dx[:, 0]) / J
-    sigma = np.where(J_theta < 0, -1.0, 1.0)
+    # KMAH index 1: J leaves the upper half plane through the negative real axis at the first
+    # caustic, where the principal square root jumps; sigma = -1 once arg J < -KMAH_ARG.  Near the
+    # source J is close to the positive real axis (take-off part ~ 0) and sigma stays +1.
+    sigma = np.where(np.angle(J) < -KMAH_ARG, -1.0, 1.0)
     amp = sigma * np.sqrt(S.rho_s * Vsn / (c['rho'] * J))
+    # Take-off measure along the line times the row/column blend.  Along a row the beam centre moves
+    # with theta as dx_c/dtheta = -b_theta/b_x, so d vartheta_c/dtheta = vartheta_theta -
+    # vartheta_x b_theta/b_x; the blend is b_x^2/|grad_x b|^2 for rows and b_z^2/|grad_x b|^2 for
+    # columns (the two add up to 1; in a homogeneous medium grad_x b is normal to the ray and this is
+    # g_z^2 and g_x^2).  Their product stays bounded where the level line of b runs along the grid
+    # line: |vartheta_theta b_l - vartheta_l b_theta| |b_l| / |grad_x b|^2.
+    g2 = c['bx'] ** 2 + c['bz'] ** 2
     if axis == 2:
-        jac = c['Tt'] - c['Tx'] * c['bt'] / c['bx']
-        wpart = (V[:, 1] / np.hypot(V[:, 0], V[:, 1])) ** 2
+        wj = np.abs(c['Tt'] * c['bx'] - c['Tx'] * c['bt']) * np.abs(c['bx']) / g2
         M, pl = Mxx, p[:, 0]
     else:
-        jac = c['Tt'] - c['Tz'] * c['bt'] / c['bz']
-        wpart = (V[:, 0] / np.hypot(V[:, 0], V[:, 1])) ** 2
+        wj = np.abs(c['Tt'] * c['bz'] - c['Tz'] * c['bt']) * np.abs(c['bz']) / g2
         M, pl = Mzz, p[:, 1]
     weight = 1j * S.c_ref ** 2 / (4 * np.pi * vs ** 2)
-    coef = S.dth * np.abs(jac) * wpart * weight * amp
+    coef = S.dth * wj * weight * amp
+    # A centre where the level-set Jacobian is singular (no finite beam) carries no weight.
+    ok = np.isfinite(coef) & np.isfinite(M)
+    coef = np.where(ok, coef, 0.0)
+    M = np.where(ok, M, 0.0)
     return c, dict(coef=coef, M=M, p=pl)
 
 
@@ -187,8 +204,7 @@ def green(S, lab, omegas, beam_width):
 
     Beams are centred where Gamma crosses the receiver's row (offset x0 - x_c along the row, the
     paper's same-depth evaluation) and where it crosses the receiver's column (offset along the
-    column, for flat rays); the two are blended by the partition of unity g_z^2 + g_x^2 = 1 of the
-    unit group direction at the centre.  Each beam adds
+    column, for flat rays); the two are blended by b_x^2/|grad b|^2 and b_z^2/|grad b|^2.  Each adds
         dtheta |d vartheta_c / d theta| w c exp(i omega (tau_c + p_l delta + M_ll delta^2 / 2))
     with c = i c_ref^2 / (4 pi v_s(vartheta)^2) sigma sqrt(rho_s |V_s| / (rho J)).
     """
@@ -208,8 +224,12 @@ def green(S, lab, omegas, beam_width):
             else:
                 zc = zg[c['iz']] + c['t'] * S.hz
                 delta = zg[None, :] - zc[:, None]
+            # Im M annihilates V, so Im M_ll >= 0 along a grid line up to discretisation error; the
+            # Gaussian factor uses max(Im M_ll, 0) so that no beam grows away from its centre
+            M = bc['M'][:, None]
+            Mc = M.real + 1j * np.maximum(M.imag, 0.0)
             ph = np.exp(1j * om * (c['tau'][:, None] + bc['p'][:, None] * delta
-                                   + 0.5 * bc['M'][:, None] * delta ** 2))
+                                   + 0.5 * Mc * delta ** 2))
             contrib = bc['coef'][:, None] * ph
             if axis == 2:
                 np.add.at(u, (c['iz'][:, None], np.arange(S.nx)[None, :]), contrib)

@@ -29,7 +29,7 @@ EGB_FP32_PHASE64, EGB_FP64 = 0, 1
 
 EXPORTED = ('egb_create', 'egb_destroy', 'egb_medium', 'egb_source', 'egb_evolve', 'egb_superpose',
             'egb_sync', 'egb_release', 'egb_last_error', 'egb_get_solve_info', 'egb_read_state',
-            'egb_read_velocity', 'egb_superpose_noalloc')
+            'egb_read_velocity', 'egb_superpose_noalloc', 'egb_evolve_batch')
 
 
 class EgbError(RuntimeError):
@@ -46,7 +46,8 @@ class egb_solve_info(ctypes.Structure):
     _fields_ = [('nx', ctypes.c_int), ('nz', ctypes.c_int), ('n_theta', ctypes.c_int),
                 ('n_omega', ctypes.c_int), ('steps_done', ctypes.c_int), ('dt', ctypes.c_double),
                 ('max_rate', ctypes.c_double), ('c_ref', ctypes.c_double),
-                ('cells', ctypes.c_uint64), ('device_bytes', ctypes.c_uint64)]
+                ('cells', ctypes.c_uint64), ('device_bytes', ctypes.c_uint64),
+                ('tile_chunk', ctypes.c_int)]
 
 
 _lib = None
@@ -69,6 +70,7 @@ def load(path: Optional[str] = None):
     lib.egb_medium.argtypes = [vp, i, P(i), P(d), P(d), vp, vp, P(u64)]
     lib.egb_source.argtypes = [vp, u64, P(d), i, P(d), d, P(i), d, P(u64)]
     lib.egb_evolve.argtypes = [vp, u64, i, d]
+    lib.egb_evolve_batch.argtypes = [vp, i, P(u64), P(i), d]
     lib.egb_superpose.argtypes = [vp, u64, vp, vp, vp, vp, i]
     lib.egb_superpose_noalloc.argtypes = [vp, u64, vp, vp, vp, vp, i]
     lib.egb_sync.argtypes = [vp]
@@ -143,6 +145,13 @@ def egb_source(h, medium, xs, omegas: Sequence[float], beam_width, n_theta, r0=0
 
 def egb_evolve(h, solve, steps, cfl):
     _check(h, load().egb_evolve(h, solve, int(steps), float(cfl)))
+
+
+def egb_evolve_batch(h, solves: Sequence[int], steps: Sequence[int], cfl):
+    n = len(solves)
+    ids = (ctypes.c_uint64 * max(n, 1))(*solves)
+    st = (ctypes.c_int * max(n, 1))(*[int(x) for x in steps])
+    _check(h, load().egb_evolve_batch(h, n, ids, st, float(cfl)))
 
 
 def egb_superpose(h, solve, u_out=None, count=None, T=None, A=None, kmax=8):

@@ -57,6 +57,8 @@ size_t free_bytes() {
 
 void free_solve(Solve *s) {
     for (auto &p : s->state) cudaFree(p);
+    for (auto &p : s->state64) cudaFree(p);
+    cudaFree(s->velp64);
     cudaFree(s->vel);
     cudaFree(s->velp);
     tma_release(*s);
@@ -71,6 +73,7 @@ void free_medium(Medium *m) {
     cudaFree(m->dadx);
     cudaFree(m->dadz);
     cudaFree(m->rho);
+    cudaFree(m->c21);
     delete m;
 }
 
@@ -87,6 +90,21 @@ egb_status latched(egb_ctx *c) {
         if (bits & DeviceErrors::NUMERIC) return fail(c, EGB_E_NUMERIC, "non-finite value produced");
         if (bits & DeviceErrors::OVERFLOW) return fail(c, EGB_E_ARRIVAL_OVERFLOW, "more arrivals or beam centres than the capacity");
     }
+    return EGB_OK;
+}
+
+egb_status ensure_desc(egb_ctx *c, int n) {
+    if (c->desc_cap >= n) return EGB_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_desc);
+    c->d_desc = nullptr;
+    c->desc_cap = 0;
+    int cap = n < 8 ? 8 : n;
+    if (cudaMalloc(&c->d_desc, (size_t)9 * cap * stage_desc_bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, EGB_E_NOMEM, "stage descriptors");
+    }
+    c->desc_cap = cap;
     return EGB_OK;
 }
 
@@ -113,6 +131,12 @@ egb_status egb_create(egb_ctx **out, int device, void *cuda_stream, const egb_op
         delete c;
         return EGB_E_CUDA;
     }
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->d_err);
+        delete c;
+        return EGB_E_CUDA;
+    }
     *out = c;
     return EGB_OK;
 }
@@ -128,6 +152,8 @@ egb_status egb_destroy(egb_ctx *c) {
         c->solves.clear();
         c->media.clear();
         cudaFree(c->d_err);
+        cudaFree(c->d_desc);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     }
     delete c;
     return EGB_OK;
@@ -159,6 +185,7 @@ egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], co
     if (e == cudaSuccess) e = cudaMalloc(&m->dadx, nodes * 21 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->dadz, nodes * 21 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->rho, nodes * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->c21, nodes * 21 * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_medium(m); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the medium"); }
     const float *dc = c21, *dr = rho;
     float *tc = nullptr, *tr = nullptr;
@@ -173,6 +200,7 @@ egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], co
         dr = tr;
     }
     if (e == cudaSuccess) e = launch_medium_prep(*m, dc, dr, c->d_err, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->c21, dc, nodes * 21 * 4, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess && (tc || tr)) e = cudaStreamSynchronize(c->stream);
     cudaFree(tc);
     cudaFree(tr);
@@ -226,23 +254,36 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     s->omega.assign(omega, omega + n_omega);
     size_t cells = (size_t)nth * g.nx * g.nz;
     size_t state_b = (size_t)NFIELD * g.field * 4;
-    size_t velp_b = (size_t)3 * g.field * 4;
-    s->bytes = 3 * state_b + cells * 6 * 4 + velp_b + g.nz * 8 + (24 + 4 * nth) * 4;
+    s->fp64 = c->opts.precision == EGB_FP64;
+    size_t velp_b = (size_t)3 * g.field * (s->fp64 ? 8 : 4);
+    size_t state64_b = (size_t)4 * g.field * 8;
+    s->bytes = (s->fp64 ? state_b + 3 * state64_b : 3 * state_b) + cells * 6 * 4 + velp_b + g.nz * 8 +
+               (24 + 4 * nth) * 4;
     if (s->bytes + (256u << 20) > free_bytes()) {
         delete s;
         return fail(c, EGB_E_NOMEM, "solve needs %zu bytes of device memory", (size_t)(s->bytes));
     }
     cudaError_t e = cudaSuccess;
-    for (auto &p : s->state)
-        if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
+    if (s->fp64) {
+        e = cudaMalloc(&s->state[0], state_b);
+        for (auto &p : s->state64)
+            if (e == cudaSuccess) e = cudaMalloc(&p, state64_b);
+        if (e == cudaSuccess) e = cudaMalloc(&s->velp64, velp_b);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->velp64, 0, velp_b, c->stream);
+    } else {
+        for (auto &p : s->state)
+            if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
+        if (e == cudaSuccess) e = cudaMalloc(&s->velp, velp_b);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->velp, 0, velp_b, c->stream);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 6 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&s->velp, velp_b);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->velp, 0, velp_b, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&s->ball, g.nz * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_solve(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
-    e = tma_prepare(*s);
-    if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "tensor maps of the stencil"); }
+    if (!s->fp64) {
+        e = tma_prepare(*s);
+        if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "tensor maps of the stencil"); }
+    }
     // frozen source ball: per row the ix range with (x - xs)^2 + (z - zs)^2 <= r0^2 (FP64)
     std::vector<int2> ball(g.nz);
     for (int iz = 0; iz < g.nz; ++iz) {
@@ -261,8 +302,13 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     e = cudaMalloc(&d_rate, 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_rate, 0, 4, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->ball, ball.data(), g.nz * sizeof(int2), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_solve_setup(*s, c->d_err, d_rate, c->stream);
-    if (e == cudaSuccess) e = launch_init_state(*s, c->stream);
+    if (s->fp64) {
+        if (e == cudaSuccess) e = launch_source_block(*s, c->stream);
+        if (e == cudaSuccess) e = fp64_setup(*s, d_rate, c->stream);
+    } else {
+        if (e == cudaSuccess) e = launch_solve_setup(*s, c->d_err, d_rate, c->stream);
+        if (e == cudaSuccess) e = launch_init_state(*s, c->stream);
+    }
     float rate = 0, cref = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&rate, d_rate, 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cref, s->src + 22, 4, cudaMemcpyDeviceToHost, c->stream);
@@ -273,6 +319,13 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     s->max_rate = rate;
     s->c_ref = cref;
     s->cur = 0;
+    if (!s->fp64) {
+        egb_status st = ensure_desc(c, 1);
+        if (st != EGB_OK) { free_solve(s); return st; }
+        s->dt = 0.5 / s->max_rate;
+        e = tma_autotune(*s, c->d_desc, c->d_err, c->stream);
+        if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "stencil autotuning"); }
+    }
     uint64_t id = c->next_id++;
     c->solves[id] = s;
     m->solves++;
@@ -289,11 +342,61 @@ egb_status egb_evolve(egb_ctx *c, egb_solve_id sid, int steps, double cfl) {
     Solve *s = it->second;
     DeviceGuard dg(c->device);
     s->dt = cfl / s->max_rate;
-    for (int i = 0; i < steps; ++i) {
-        cudaError_t e = launch_rk3_step_tma(*s, (float)s->dt, c->d_err, c->stream);
+    if (s->fp64) {
+        for (int i = 0; i < steps; ++i) {
+            cudaError_t e = launch_rk3_step64(*s, s->dt, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "evolve launch");
+        }
+    } else {
+        egb_status st = ensure_desc(c, 1);
+        if (st != EGB_OK) return st;
+        Solve *one[1] = {s};
+        cudaError_t e = evolve_batch(one, 1, steps, c->d_desc, c->d_err, c->stream, c->cap_stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "evolve launch");
     }
     s->steps += steps;
+    return EGB_OK;
+}
+
+egb_status egb_evolve_batch(egb_ctx *c, int n, const egb_solve_id *ids, const int *steps, double cfl) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (n < 0 || (n > 0 && (!ids || !steps))) return fail(c, EGB_E_INVALID, "bad batch arguments");
+    if (!(cfl > 0) || cfl > 1) return fail(c, EGB_E_INVALID, "0 < cfl <= 1 required");
+    std::vector<Solve *> sv(n);
+    std::vector<int> left(n);
+    for (int i = 0; i < n; ++i) {
+        auto it = c->solves.find(ids[i]);
+        if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id in batch");
+        if (it->second->fp64) return fail(c, EGB_E_INVALID, "FP64-form solves cannot be batched");
+        if (steps[i] < 0) return fail(c, EGB_E_INVALID, "steps must be >= 0");
+        for (int j = 0; j < i; ++j)
+            if (sv[j] == it->second) return fail(c, EGB_E_INVALID, "a solve appears twice in the batch");
+        sv[i] = it->second;
+        left[i] = steps[i];
+        sv[i]->dt = cfl / sv[i]->max_rate;
+    }
+    DeviceGuard dg(c->device);
+    egb_status st = ensure_desc(c, n);
+    if (st != EGB_OK) return st;
+    // advance all unfinished solves by the smallest remaining count, drop the finished, repeat
+    while (true) {
+        std::vector<Solve *> act;
+        int m = 0;
+        for (int i = 0; i < n; ++i)
+            if (left[i] > 0) {
+                act.push_back(sv[i]);
+                m = (m == 0 || left[i] < m) ? left[i] : m;
+            }
+        if (act.empty()) break;
+        cudaError_t e = evolve_batch(act.data(), (int)act.size(), m, c->d_desc, c->d_err, c->stream, c->cap_stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batched evolve");
+        for (int i = 0; i < n; ++i)
+            if (left[i] > 0) {
+                left[i] -= m;
+                sv[i]->steps += m;
+            }
+    }
     return EGB_OK;
 }
 
@@ -331,6 +434,7 @@ egb_status egb_superpose(egb_ctx *c, egb_solve_id sid, void *u_out, uint8_t *cou
     if (e == cudaSuccess && hc) e = cudaMalloc(&dc, nodes);
     if (e == cudaSuccess && hT) e = cudaMalloc(&dT, nodes * kmax * 8);
     if (e == cudaSuccess && hA) e = cudaMalloc(&dA, nodes * kmax * 4);
+    if (e == cudaSuccess && s->fp64) e = fp64_to_fp32_state(*s, c->stream);
     if (e == cudaSuccess)
         e = launch_superpose(*s, (float2 *)du, dc, dT, dA, kmax, c->d_err, c->stream);
     if (e == cudaSuccess && hu) e = cudaMemcpyAsync(u_out, du, ub, cudaMemcpyDeviceToHost, c->stream);
@@ -423,6 +527,7 @@ egb_status egb_get_solve_info(egb_ctx *c, egb_solve_id sid, egb_solve_info *out)
     out->c_ref = s->c_ref;
     out->cells = (uint64_t)s->g.nth * s->g.nx * s->g.nz;
     out->device_bytes = s->bytes + s->scratch_bytes;
+    out->tile_chunk = s->fp64 ? 0 : tma_chunk(*s);
     return EGB_OK;
 }
 
@@ -438,7 +543,7 @@ egb_status egb_read_state(egb_ctx *c, egb_solve_id sid, double *out) {
     bool host = !is_device_ptr(out);
     cudaError_t e = cudaSuccess;
     if (host) e = cudaMalloc(&d, bytes);
-    if (e == cudaSuccess) e = launch_read_state(*s, d, c->stream);
+    if (e == cudaSuccess) e = s->fp64 ? launch_read_state64(*s, d, c->stream) : launch_read_state(*s, d, c->stream);
     if (e == cudaSuccess && host) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (host) cudaFree(d);

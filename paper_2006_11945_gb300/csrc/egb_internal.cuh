@@ -84,6 +84,7 @@ struct Medium {
     float *dadx = nullptr;  // [21][nz][nx]
     float *dadz = nullptr;  // [21][nz][nx]
     float *rho = nullptr;   // [nz][nx]
+    float *c21 = nullptr;   // [nz*nx][21] device copy of the input stiffness
     int solves = 0;
     size_t bytes = 0;
 };
@@ -99,6 +100,9 @@ struct Solve {
     float *vel = nullptr;   // [6][nth][nz][nx]: Vx, Vz, thetadot, v, pdx, pdz
     float *velp = nullptr;  // [3][nth][nz+4][pitch]: Vx, Vz, thetadot in the padded state layout
     void *tma = nullptr;    // tensor maps of the TMA stencil
+    bool fp64 = false;      // plain all-FP64 form
+    double *state64[3] = {nullptr, nullptr, nullptr};  // [4 fields] Yx, Yz, vartheta, tau (FP64 form)
+    double *velp64 = nullptr;                           // [3] padded Vx, Vz, thetadot (FP64 form)
     int2 *ball = nullptr;   // [nz] frozen ix range per row (lo > hi: none)
     float *src = nullptr;   // source block: a_s[21], rho_s, c_ref, then [nth] x (psx, psz)
     float *scratch = nullptr;  // superposition scratch (lazily sized)
@@ -107,6 +111,8 @@ struct Solve {
     int steps = 0;
     size_t bytes = 0;
 };
+
+struct StageDesc;  // per-solve, per-stage descriptor of the batched stencil (liouville_tma.cu)
 
 struct Ctx {
     int device;
@@ -118,6 +124,9 @@ struct Ctx {
     std::unordered_map<uint64_t, Medium *> media;
     std::unordered_map<uint64_t, Solve *> solves;
     unsigned *d_err = nullptr;  // device error bits
+    StageDesc *d_desc = nullptr;  // stage descriptors of batched launches (device)
+    int desc_cap = 0;             // capacity in solves (9 descriptors per solve)
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -128,7 +137,11 @@ cudaError_t launch_init_state(const Solve &sv, cudaStream_t s);
 cudaError_t launch_rk3_step(Solve &sv, float dt, cudaStream_t s);
 cudaError_t tma_prepare(Solve &sv);
 void tma_release(Solve &sv);
-cudaError_t launch_rk3_step_tma(Solve &sv, float dt, unsigned *d_err, cudaStream_t s);
+size_t stage_desc_bytes();
+int tma_chunk(const Solve &sv);
+cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s);
+cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
+                         cudaStream_t cap);
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 size_t superpose_scratch_bytes(const Solve &sv);
@@ -136,5 +149,10 @@ size_t superpose_scratch_bytes(const Solve &sv);
 // must be the current device; looked up once per device.
 cudaError_t noalloc_scratch(int device, void **ptr);
 cudaError_t launch_read_state(const Solve &sv, double *out_dev, cudaStream_t s);
+cudaError_t launch_source_block(const Solve &sv, cudaStream_t s);
+cudaError_t fp64_setup(Solve &sv, float *d_rate, cudaStream_t s);
+cudaError_t launch_rk3_step64(Solve &sv, double dt, cudaStream_t s);
+cudaError_t fp64_to_fp32_state(Solve &sv, cudaStream_t s);
+cudaError_t launch_read_state64(const Solve &sv, double *out_dev, cudaStream_t s);
 
 }  // namespace egb

@@ -32,14 +32,18 @@ constexpr size_t SMEM_BYTES = sizeof(float) * ((size_t)RING * HALO_FLOATS + (siz
 constexpr int THREADS = 256;
 }  // namespace tma
 
-struct TmaArgs {
-    Grid2D g;
+// One solve, one RK stage.  Lives in device memory; a launch processes the work items of several
+// solves (batching), item i of solve s being item i - item_begin of that solve.
+struct StageDesc {
+    const CUtensorMap *mapK;  // halo map of the state being differentiated (device address)
+    const CUtensorMap *mapN;  // interior map of u^n
+    const CUtensorMap *mapV;  // interior map of the padded velocities
     float *out;
     const int2 *ball;
+    Grid2D g;
     float dt, coef, ihx, ihz, idth;
     float eps[4];
-    int tiles_x, tiles_z, chunk, nchunks, items;
-    unsigned *err;
+    int tiles_x, tiles_z, chunk, items, item_begin;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -130,8 +134,7 @@ __device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5]
 
 template <int STAGE>
 __global__ void __launch_bounds__(tma::THREADS, 1)
-    k_rk3_tma(const __grid_constant__ CUtensorMap mapK, const __grid_constant__ CUtensorMap mapN,
-              const __grid_constant__ CUtensorMap mapV, TmaArgs A) {
+    k_rk3_tma(const StageDesc *__restrict__ D, int nsolves, int total_items, unsigned *err) {
     using namespace tma;
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = reinterpret_cast<float *>(smem);
@@ -139,7 +142,6 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
     uint64_t *bar = reinterpret_cast<uint64_t *>(ring2 + RING2 * SLOT2_FLOATS);
     uint64_t *bar2 = bar + RING;
     __shared__ int abort_flag;
-    const Grid2D &g = A.g;
     const int tid = threadIdx.x;
     const int tx = tid & 31, tz = tid >> 5;
     if (tid == 0) {
@@ -152,9 +154,14 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
     uint32_t pending = 0, pending2 = 0;  // slots with a copy in flight (thread 0 only)
     const uint32_t bytes_halo = HALO_FLOATS * 4;
     const uint32_t bytes2 = (STAGE == 1 ? V_FLOATS : SLOT2_FLOATS) * 4;
-    const int64_t F = g.field;
+    int si = 0;
 
-    for (int item = blockIdx.x; item < A.items; item += gridDim.x) {
+    for (int gitem = blockIdx.x; gitem < total_items; gitem += gridDim.x) {
+        while (si + 1 < nsolves && gitem >= D[si + 1].item_begin) ++si;
+        const StageDesc &A = D[si];
+        const Grid2D &g = A.g;
+        const int64_t F = g.field;
+        const int item = gitem - A.item_begin;
         int xt = item % A.tiles_x;
         int rest = item / A.tiles_x;
         int zt = rest % A.tiles_z;
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
         auto issue = [&](int j) {
             int s = j % RING;
             mbar_expect_tx(bar + s, bytes_halo);
-            tma_load_4d(ring + s * HALO_FLOATS, &mapK, x0, z0, plane_of(j), 0, bar + s);
+            tma_load_4d(ring + s * HALO_FLOATS, A.mapK, x0, z0, plane_of(j), 0, bar + s);
             pending |= 1u << s;
         };
         auto issue2 = [&](int j) {
@@ -175,8 +182,8 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
             mbar_expect_tx(bar2 + s, bytes2);
             float *dst = ring2 + s * SLOT2_FLOATS;
             int k = k0 + j;
-            if (STAGE != 1) tma_load_4d(dst, &mapN, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
-            tma_load_4d(dst + UN_FLOATS, &mapV, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
+            if (STAGE != 1) tma_load_4d(dst, A.mapN, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
+            tma_load_4d(dst + UN_FLOATS, A.mapV, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
             pending2 |= 1u << s;
         };
         if (tid == 0) {
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
     if (abort_flag) {
         // latch the timeout and drain the copies this CTA still has in flight (bounded)
         if (tid == 0) {
-            atomicOr(A.err, DeviceErrors::TIMEOUT);
+            atomicOr(err, DeviceErrors::TIMEOUT);
             for (int s = 0; s < RING; ++s)
                 if (pending & (1u << s)) mbar_wait_bounded(bar + s, (phase >> s) & 1u);
             for (int s = 0; s < RING2; ++s)
@@ -347,8 +354,21 @@ static cudaError_t make_map(CUtensorMap *m, const Grid2D &g, float *base, int nf
 }
 
 struct TmaMaps {
-    CUtensorMap halo[3], inner[3], vel;
+    CUtensorMap halo[3], inner[3], vel;  // host copies
+    CUtensorMap *dev = nullptr;          // device copies: halo[0..2], inner[0..2], vel
+    int chunk = 0;                       // theta-chunk length chosen by the autotuner
 };
+
+static const CUtensorMap *dmap_halo(const Solve &sv, int b) { return ((TmaMaps *)sv.tma)->dev + b; }
+static const CUtensorMap *dmap_inner(const Solve &sv, int b) { return ((TmaMaps *)sv.tma)->dev + 3 + b; }
+static const CUtensorMap *dmap_vel(const Solve &sv) { return ((TmaMaps *)sv.tma)->dev + 6; }
+
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
 
 cudaError_t tma_prepare(Solve &sv) {
     TmaMaps *m = new TmaMaps();
@@ -358,7 +378,13 @@ cudaError_t tma_prepare(Solve &sv) {
         if (e == cudaSuccess) e = make_map(&m->inner[b], sv.g, sv.state[b], NFIELD, tma::TX, tma::TZ);
     }
     if (e == cudaSuccess) e = make_map(&m->vel, sv.g, sv.velp, 3, tma::TX, tma::TZ);
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev, 7 * sizeof(CUtensorMap));
+    if (e == cudaSuccess) {
+        CUtensorMap all[7] = {m->halo[0], m->halo[1], m->halo[2], m->inner[0], m->inner[1], m->inner[2], m->vel};
+        e = cudaMemcpy(m->dev, all, sizeof all, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
+        cudaFree(m->dev);
         delete m;
         return e;
     }
@@ -376,17 +402,18 @@ cudaError_t tma_prepare(Solve &sv) {
 }
 
 void tma_release(Solve &sv) {
+    if (sv.tma) cudaFree(((TmaMaps *)sv.tma)->dev);
     delete (TmaMaps *)sv.tma;
     sv.tma = nullptr;
 }
 
-cudaError_t launch_rk3_step_tma(Solve &sv, float dt, unsigned *d_err, cudaStream_t s) {
+// Stage descriptor of solve `sv` for step r of a 3-step rotation starting at buffer cur0.
+static StageDesc make_desc(const Solve &sv, int stage, int r, int chunk) {
     const Grid2D &g = sv.g;
-    TmaMaps *maps = (TmaMaps *)sv.tma;
-    TmaArgs A;
+    StageDesc A;
     A.g = g;
     A.ball = sv.ball;
-    A.dt = dt;
+    A.dt = (float)sv.dt;
     A.ihx = (float)(1.0 / g.hx);
     A.ihz = (float)(1.0 / g.hz);
     A.idth = (float)(1.0 / g.dth);
@@ -396,33 +423,106 @@ cudaError_t launch_rk3_step_tma(Solve &sv, float dt, unsigned *d_err, cudaStream
     A.eps[3] = (float)(1e-6 * (h / sv.c_ref) * (h / sv.c_ref));
     A.tiles_x = (g.nx + tma::TX - 1) / tma::TX;
     A.tiles_z = (g.nz + tma::TZ - 1) / tma::TZ;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long tiles = (long)A.tiles_x * A.tiles_z;
-    long want = (long)g.nth * tiles / (4L * sms);
-    int chunk = (int)(want < 8 ? 8 : (want > 64 ? 64 : want));
-    if (chunk > g.nth) chunk = g.nth;
-    A.chunk = chunk;
-    A.nchunks = (g.nth + chunk - 1) / chunk;
-    A.items = (int)(tiles * A.nchunks);
-    A.err = d_err;
-    int grid = A.items < sms ? A.items : sms;
-    int n = sv.cur, b1 = (sv.cur + 1) % 3, b2 = (sv.cur + 2) % 3;
-    // stage 1: u1 = u + dt L(u)
-    A.out = sv.state[b1];
-    A.coef = 1.f;
-    k_rk3_tma<1><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(maps->halo[n], maps->inner[n], maps->vel, A);
-    // stage 2: u2 = u + 1/4 ((u1 - u) + dt L(u1))
-    A.out = sv.state[b2];
-    A.coef = 0.25f;
-    k_rk3_tma<2><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(maps->halo[b1], maps->inner[n], maps->vel, A);
-    // stage 3: u_new = u + 2/3 ((u2 - u) + dt L(u2))
-    A.out = sv.state[b1];
-    A.coef = 2.f / 3.f;
-    k_rk3_tma<3><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(maps->halo[b2], maps->inner[n], maps->vel, A);
-    sv.cur = b1;
+    A.chunk = chunk > g.nth ? g.nth : chunk;
+    A.items = A.tiles_x * A.tiles_z * ((g.nth + A.chunk - 1) / A.chunk);
+    A.item_begin = 0;
+    int n = (sv.cur + r) % 3, b1 = (n + 1) % 3, b2 = (n + 2) % 3;
+    A.mapN = dmap_inner(sv, n);
+    A.mapV = dmap_vel(sv);
+    if (stage == 1) { A.mapK = dmap_halo(sv, n);  A.out = sv.state[b1]; A.coef = 1.f; }
+    if (stage == 2) { A.mapK = dmap_halo(sv, b1); A.out = sv.state[b2]; A.coef = 0.25f; }
+    if (stage == 3) { A.mapK = dmap_halo(sv, b2); A.out = sv.state[b1]; A.coef = 2.f / 3.f; }
+    return A;
+}
+
+static void launch_stage(int stage, const StageDesc *d, int nsolves, int total, unsigned *err, cudaStream_t s) {
+    int sms = sm_count();
+    int grid = total < sms ? total : sms;
+    if (grid < 1) return;
+    if (stage == 1) k_rk3_tma<1><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);
+    if (stage == 2) k_rk3_tma<2><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);
+    if (stage == 3) k_rk3_tma<3><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);
+}
+
+int tma_chunk(const Solve &sv) { return sv.tma ? ((TmaMaps *)sv.tma)->chunk : 0; }
+
+// Autotuner: time stage 1 (reads u^n, writes a stage buffer, so the state is untouched) for each
+// theta-chunk candidate and keep the fastest.  Synchronises the stream.
+cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s) {
+    static const int cand[4] = {8, 16, 32, 64};
+    float best = 1e30f;
+    int best_chunk = 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int ci = 0; ci < 4; ++ci) {
+        int ch = cand[ci];
+        if (ch > sv.g.nth && ci > 0) break;
+        StageDesc h = make_desc(sv, 1, 0, ch);
+        cudaMemcpyAsync(d_desc, &h, sizeof h, cudaMemcpyHostToDevice, s);
+        launch_stage(1, d_desc, 1, h.items, err, s);  // warm
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep) launch_stage(1, d_desc, 1, h.items, err, s);
+        cudaEventRecord(e1, s);
+        cudaError_t er = cudaEventSynchronize(e1);
+        if (er != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return er; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_chunk = ch; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ((TmaMaps *)sv.tma)->chunk = best_chunk;
     return cudaGetLastError();
 }
+
+// Advance several FP32 solves together: per stage one persistent launch over the work items of all
+// of them.  Whole 3-step rotations are captured once into a CUDA graph and replayed; the rest are
+// launched directly.  d_desc must hold 9 * n descriptors; cap is a non-legacy stream for capture.
+cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
+                         cudaStream_t cap) {
+    if (n <= 0 || steps <= 0) return cudaSuccess;
+    std::vector<StageDesc> h((size_t)9 * n);
+    int total[9];
+    for (int r = 0; r < 3; ++r)
+        for (int st = 1; st <= 3; ++st) {
+            int slot = r * 3 + (st - 1);
+            int begin = 0;
+            for (int i = 0; i < n; ++i) {
+                StageDesc d = make_desc(*sv[i], st, r, tma_chunk(*sv[i]) ? tma_chunk(*sv[i]) : 16);
+                d.item_begin = begin;
+                begin += d.items;
+                h[(size_t)slot * n + i] = d;
+            }
+            total[slot] = begin;
+        }
+    cudaError_t e = cudaMemcpyAsync(d_desc, h.data(), h.size() * sizeof(StageDesc), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    auto run_step = [&](int r, cudaStream_t st) {
+        for (int stage = 1; stage <= 3; ++stage) {
+            int slot = r * 3 + (stage - 1);
+            launch_stage(stage, d_desc + (size_t)slot * n, n, total[slot], err, st);
+        }
+    };
+    int rotations = steps / 3, rest = steps % 3;
+    if (rotations > 0) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        for (int r = 0; r < 3; ++r) run_step(r, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int i = 0; i < rotations && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, s);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return e;
+    }
+    for (int r = 0; r < rest; ++r) run_step(r, s);
+    for (int i = 0; i < n; ++i) sv[i]->cur = (sv[i]->cur + steps) % 3;
+    return cudaGetLastError();
+}
+
+size_t stage_desc_bytes() { return sizeof(StageDesc); }
 
 }  // namespace egb

@@ -175,6 +175,11 @@ __global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, fl
     }
 }
 
+cudaError_t launch_source_block(const Solve &sv, cudaStream_t s) {
+    k_source<<<(sv.g.nth + 127) / 128, 128, 0, s>>>(*sv.m, sv.xs, sv.zs, sv.g.nth, sv.src);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, cudaStream_t s) {
     (void)d_err;
     k_source<<<(sv.g.nth + 127) / 128, 128, 0, s>>>(*sv.m, sv.xs, sv.zs, sv.g.nth, sv.src);

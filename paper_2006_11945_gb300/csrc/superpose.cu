@@ -12,7 +12,7 @@
 //                  reduced mod 2 pi in double-float (Cody & Waite's split-constant reduction)
 //  k_sum           per receiver: sum over angles of the beams centred on its row (offset along x:
 //                  the paper's same-depth evaluation) and on its column (offset along z, for flat
-//                  rays), blended by g_z^2 + g_x^2 = 1                                      (Eq. 34)
+//                  rays), blended by b_x^2/|grad b|^2 + b_z^2/|grad b|^2 = 1                (Eq. 34)
 //  k_arrivals      per receiver: sign changes of b along theta -> traveltime and geometrical
 //                  amplitude of every arrival, late arrivals included
 #include "christoffel.cuh"
@@ -201,21 +201,19 @@ __global__ void k_centres(SupArgs A) {
         float vth = cth * Vx - sth * Vz;
         float iv2 = 1.f / (v * v);
         float dpth_x = (cth * v - sth * vth) * iv2, dpth_z = (-sth * v - cth * vth) * iv2;
-        float Jt = dT[0] * Vz - dT[1] * Vx;
-        float sigma = Jt < 0.f ? -1.f : 1.f;
-        float Vn = sqrtf(Vx * Vx + Vz * Vz);
-        float jac, wpart, pl, pos;
+        // take-off measure times the row/column blend b_l^2 / |grad b|^2 (bounded where the level
+        // line of b runs along the grid line): |vartheta_theta b_l - vartheta_l b_theta| |b_l| / |grad b|^2
+        float g2 = bx * bx + bz * bz;
+        float wj, pl, pos;
         if (ROW) {
-            jac = tt - tx * bt / bx;
-            wpart = (Vz / Vn) * (Vz / Vn);
+            wj = fabsf(tt * bx - tx * bt) * fabsf(bx) / g2;
             pl = pxl;
         } else {
-            jac = tt - tz * bt / bz;
-            wpart = (Vx / Vn) * (Vx / Vn);
+            wj = fabsf(tt * bz - tz * bt) * fabsf(bz) / g2;
             pl = pzl;
         }
         pos = (float)((double)i * h) + t * h;
-        float wreal = g.dth * fabsf(jac) * wpart * c_ref * c_ref / (4.f * 3.14159265358979f * sv.v * sv.v);
+        float wreal = g.dth * wj * c_ref * c_ref / (4.f * 3.14159265358979f * sv.v * sv.v);
         int64_t slot = slot0 + cnt;
         (ROW ? A.rpos : A.cpos)[slot] = pos;
         (ROW ? A.rp : A.cp)[slot] = pl;
@@ -231,6 +229,10 @@ __global__ void k_centres(SupArgs A) {
             cf M;
             if (ROW) M = cdiv(cf{dpx.re * Vz - pdx * dz.re, dpx.im * Vz - pdx * dz.im}, J);
             else M = cdiv(cf{-dpz.re * Vx + pdz * dx.re, -dpz.im * Vx + pdz * dx.im}, J);
+            // KMAH index 1: at the first caustic J leaves the upper half plane through the negative
+            // real axis, where the principal root jumps; sigma = -1 once arg J < -1e-3 (near the
+            // source J is close to the positive real axis and sigma stays +1)
+            float sigma = atan2f(J.im, J.re) < -1e-3f ? -1.f : 1.f;
             cf amp = csqrt_pr(cdiv(cf{rho_s * sv.Vn / rho, 0.f}, J));
             // coef = i * wreal * sigma * amp
             cf coef = {-wreal * sigma * amp.im, wreal * sigma * amp.re};
@@ -239,7 +241,15 @@ __global__ void k_centres(SupArgs A) {
             float sp, cp;
             sincosf(ph, &sp, &cp);
             cf E = cmul(coef, cf{cp, sp});
-            (ROW ? A.rdat : A.cdat)[(int64_t)w * lines_total + slot] = make_float4(E.re, E.im, M.re, M.im);
+            // a centre where the level-set Jacobian is singular (no finite beam) carries no weight
+            if (!(isfinite(E.re) && isfinite(E.im) && isfinite(M.re) && isfinite(M.im))) {
+                E = cf{0.f, 0.f};
+                M = cf{0.f, 0.f};
+            }
+            // Im M annihilates V, so Im M_ll >= 0 along a grid line up to discretisation error; the
+            // Gaussian factor uses max(Im M_ll, 0) so that no beam grows away from its centre
+            (ROW ? A.rdat : A.cdat)[(int64_t)w * lines_total + slot] =
+                make_float4(E.re, E.im, M.re, fmaxf(M.im, 0.f));
         }
         ++cnt;
     }
@@ -394,7 +404,7 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
     };
     SupArgs A;
     A.g = g;
-    A.st = sv.state[sv.cur];
+    A.st = sv.fp64 ? sv.state[0] : sv.state[sv.cur];  // the FP64 form converts into buffer 0
     A.vel = sv.vel;
     A.rho = sv.m->rho;
     A.src = sv.src;

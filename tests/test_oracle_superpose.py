@@ -105,3 +105,14 @@ def test_vti_far_field_matches_plane_wave_integral(vti):
     assert np.max(np.abs(Ta[..., 0][sel] - T) / T) < 2e-4
     Aref = np.abs(ref) * math.sqrt(om)
     assert np.max(np.abs(A[..., 0][sel] - Aref) / Aref) < 2e-3
+
+
+def test_heterogeneous_wavefield_is_bounded():
+    """In a heterogeneous TTI medium every beam that enters the sum decays along its evaluation
+    line, so the Green's function stays of the order of the homogeneous one (no runaway Gaussians)."""
+    p = synthmedia.tti_heterogeneous(n=80, n_theta=48, length=2560.0, steps=220, freqs=(10.0, 20.0))
+    S, st, dt = L.evolve(p)
+    lab = L.interior_state(st, S)
+    u = SP.green(S, lab, p.omegas, p.beam_width)
+    assert np.all(np.isfinite(u))
+    assert np.max(np.abs(u)) < 1.0
