@@ -341,13 +341,65 @@ def run_reference(args):
     }))
 
 
+def serve_requests(duration, seed=4, rate=200.0, large_scale=1.0):
+    """The Poisson request stream (50/50 small/large, 1-8 frequencies in 8-40 Hz) as Requests."""
+    import dataclasses
+    from paper_2006_11945_gb300.serve import Request
+    out = []
+    media = {}
+    small = synthmedia.vti_homogeneous()
+    for i, (t, kind, nf, freqs) in enumerate(synthmedia.request_stream(rate=rate, duration=duration,
+                                                                       seed=seed)):
+        if kind == 'small':
+            p = dataclasses.replace(small, freqs=list(freqs))
+        else:
+            # eight seeded large media, reused across requests (building one takes seconds on the host)
+            key = i % 8
+            if key not in media:
+                n = int(512 * large_scale) // 4 * 4
+                media[key] = synthmedia.tti_heterogeneous(n=n, h=2560.0 / n,
+                                                          n_theta=max(16, int(256 * large_scale)),
+                                                          seed=100 + key)
+            p = dataclasses.replace(media[key], freqs=list(freqs))
+        out.append(Request(i, t, p))
+    return out
+
+
+def run_serve(args):
+    """Serving measurement: arrivals for --serve-seconds, then drain what was admitted."""
+    import torch
+    from paper_2006_11945_gb300.serve import Backend, serve
+    torch.cuda.set_device(0)
+    reqs = serve_requests(args.serve_seconds, large_scale=args.serve_large_scale)
+    be = Backend(0)
+    st = serve(reqs, be, chunk_steps=args.serve_chunk, time_limit=args.serve_seconds)
+    be.close()
+    s = st.summary(len(reqs))
+    small = [r.finished - r.arrival for r in st.completed if r.problem.name == 'vti_homogeneous']
+    large = [r.finished - r.arrival for r in st.completed if r.problem.name != 'vti_homogeneous']
+    for name, lat in (('small', small), ('large', large)):
+        if lat:
+            s[f'{name}_p50_s'] = float(np.percentile(lat, 50))
+            s[f'{name}_p99_s'] = float(np.percentile(lat, 99))
+            s[f'{name}_completed'] = len(lat)
+    print(json.dumps({'metric': 'serving: solves/s and p50/p99 latency', 'value': s['solves_per_s'],
+                      'unit': 'solves/s', 'higher_is_better': True,
+                      'config': {'workload': f'Poisson 200 req/s for {args.serve_seconds} s, 50/50 '
+                                             f'64x64x64 VTI / {int(512 * args.serve_large_scale)}^2 TTI, '
+                                             f'1-8 frequencies', 'chunk_steps': args.serve_chunk},
+                      'serving': s}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=3)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
-    ap.add_argument('--workload', default='tti512', choices=['tti512', 'tti256', 'tti128', 'vti64'])
+    ap.add_argument('--workload', default='tti512', choices=['tti512', 'tti256', 'tti128', 'vti64', 'serve'])
+    ap.add_argument('--serve-seconds', type=float, default=2.0)
+    ap.add_argument('--serve-large-scale', type=float, default=1.0)
+    ap.add_argument('--serve-chunk', type=int, default=60)
     ap.add_argument('--evolve-steps', type=int, default=None)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--cpu-seconds', type=float, default=20.0)
@@ -356,6 +408,8 @@ def main():
     args = ap.parse_args()
     if args.impl == 'reference':
         run_reference(args)
+    elif args.workload == 'serve':
+        run_serve(args)
     else:
         run_egb(args)
 

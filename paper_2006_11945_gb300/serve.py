@@ -1,0 +1,160 @@
+"""Continuous-batching request loop over the egb C ABI.
+
+Requests (a medium plus a source description) arrive over time.  The loop admits them while the
+library accepts new solves (egb_source refuses with EGB_E_NOMEM when free device memory is short;
+the request then waits), keeps every admitted solve resident on the device, and advances all of
+them together in chunks of pseudo-time steps with egb_evolve_batch, so requests that arrive while
+others are on the GPU join at the next chunk boundary and their work overlaps on the device.  When a
+solve has taken all its steps it is superposed, its results are copied out and its memory is freed,
+which admits waiting requests.  Latency = completion time - arrival time.
+
+The loop only schedules; every step of the method runs in the CUDA library.  `Backend` wraps the
+library calls so that the scheduling logic can also be driven by a fake backend on the CPU.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds since the start of the stream
+    problem: object         # synthmedia.Problem2D
+    kmax: int = 8
+    # filled by the loop
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    result: object = None
+    steps_left: int = 0
+    medium: int = 0
+    solve: int = 0
+
+
+class NoMemory(Exception):
+    """The backend refused a new solve for lack of device memory."""
+
+
+class Backend:
+    """The egb library behind the loop (one context, one CUDA stream)."""
+
+    def __init__(self, device=0, stream=0):
+        import paper_2006_11945_gb300 as egb
+        self.egb = egb
+        self.ctx = egb.Context(device, stream)
+
+    def admit(self, req: Request):
+        egb = self.egb
+        p = req.problem
+        try:
+            m = self.ctx.medium_2d(p)
+        except egb.EgbError as e:
+            if e.status == egb.EGB_E_NOMEM:
+                raise NoMemory() from e
+            raise
+        try:
+            s = self.ctx.source_2d(m, p)
+        except egb.EgbError as e:
+            egb.egb_release(self.ctx.h, m)
+            if e.status == egb.EGB_E_NOMEM:
+                raise NoMemory() from e
+            raise
+        req.medium, req.solve = m, s
+
+    def evolve(self, reqs: List[Request], steps: List[int], cfl: float):
+        self.egb.egb_evolve_batch(self.ctx.h, [r.solve for r in reqs], steps, cfl)
+
+    def finish(self, req: Request):
+        p = req.problem
+        res = self.ctx.superpose(req.solve, len(p.freqs), p.nz, p.nx, req.kmax)
+        self.egb.egb_sync(self.ctx.h)
+        self.egb.egb_release(self.ctx.h, req.solve)
+        self.egb.egb_release(self.ctx.h, req.medium)
+        return res
+
+    def close(self):
+        self.ctx.close()
+
+
+@dataclass
+class ServeStats:
+    completed: List[Request] = field(default_factory=list)
+    refused_admissions: int = 0
+    chunks: int = 0
+    max_active: int = 0
+    wall: float = 0.0
+
+    def summary(self, offered: int):
+        lat = np.array([r.finished - r.arrival for r in self.completed]) if self.completed else np.zeros(0)
+        cells = sum(r.problem.cells * r.problem.steps for r in self.completed)
+        return {
+            'offered': offered, 'completed': len(self.completed),
+            'solves_per_s': len(self.completed) / self.wall if self.wall > 0 else 0.0,
+            'cell_updates_per_s': cells / self.wall if self.wall > 0 else 0.0,
+            'p50_latency_s': float(np.percentile(lat, 50)) if lat.size else None,
+            'p99_latency_s': float(np.percentile(lat, 99)) if lat.size else None,
+            'max_active': self.max_active, 'chunks': self.chunks,
+            'refused_admissions': self.refused_admissions, 'wall_s': self.wall,
+        }
+
+
+def serve(requests: List[Request], backend, chunk_steps: int = 30, cfl: float = 0.5,
+          time_limit: Optional[float] = None, clock: Callable[[], float] = time.perf_counter,
+          max_active: Optional[int] = None) -> ServeStats:
+    """Run the request stream through the backend; returns the statistics.
+
+    Arrival times are honoured against `clock` (requests become visible once the wall time since
+    the start reaches their arrival).  With `time_limit`, no request is admitted after that time
+    and the loop returns once the admitted ones are done.
+    """
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    waiting: deque = deque()
+    active: List[Request] = []
+    stats = ServeStats()
+    t0 = clock()
+    while pending or waiting or active:
+        now = clock() - t0
+        while pending and pending[0].arrival <= now:
+            waiting.append(pending.popleft())
+        admitting = time_limit is None or now < time_limit
+        if not admitting:
+            pending.clear()
+            waiting.clear()
+        # admission by free device memory
+        while admitting and waiting and (max_active is None or len(active) < max_active):
+            req = waiting[0]
+            try:
+                backend.admit(req)
+            except NoMemory:
+                stats.refused_admissions += 1
+                break
+            waiting.popleft()
+            req.admitted = clock() - t0
+            req.steps_left = req.problem.steps
+            active.append(req)
+        stats.max_active = max(stats.max_active, len(active))
+        if not active:
+            if pending:
+                # idle until the next arrival
+                nxt = pending[0].arrival
+                while clock() - t0 < nxt:
+                    time.sleep(min(1e-3, max(0.0, nxt - (clock() - t0))))
+            continue
+        steps = [min(chunk_steps, r.steps_left) for r in active]
+        backend.evolve(active, steps, cfl)
+        stats.chunks += 1
+        for r, s in zip(active, steps):
+            r.steps_left -= s
+        done = [r for r in active if r.steps_left <= 0]
+        active = [r for r in active if r.steps_left > 0]
+        for r in done:
+            r.result = backend.finish(r)
+            r.finished = clock() - t0
+            stats.completed.append(r)
+    stats.wall = clock() - t0
+    return stats
