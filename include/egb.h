@@ -90,7 +90,9 @@ egb_status egb_medium(egb_ctx *ctx, int dim, const int n[3], const double h[3],
  *   beam_width  w0 (m, > 0): the Gaussian beams' 1/e half-width along the wavefront at the source
  *               (the complex initial data of Eq. 24)
  *   n_ang       {n_theta, unused}: phase-angle samples (8..4096)
- *   r0          radius (m) of the frozen source ball; <= 0 selects 2*max(hx, hz)
+ *   r0          radius (m) of the frozen source ball; <= 0 selects 2*max(hx, hz).  Cells within
+ *               R_Sigma = max(4 r0, min(Lx, Lz)/8) of x_s whose ray still approaches the source are
+ *               frozen too (the closest-approach manifold that replaces Eq. 20's initial plane)
  * Allocates the phase-space state (about 3 x 20 + 24 bytes per cell) after checking free device
  * memory (EGB_E_NOMEM otherwise), computes the characteristic velocities (Eqs. 3-12), the time
  * step bound and the initial level sets.  Synchronises the context stream once (to read the CFL
@@ -172,8 +174,9 @@ typedef struct {
 egb_status egb_get_solve_info(egb_ctx *ctx, egb_solve_id solve, egb_solve_info *out);
 
 /* Copy the level sets of a solve to the caller: out = [4][n_theta][nz][nx] float64 holding
- * Yx, Yz (position label minus x_s), vartheta, tau, host or device.  Synchronous.  For tests and
- * diagnostics (the state otherwise stays on the device). */
+ * b (signed distance of the ray from x_s at closest approach, m), q (1 where the labels come from
+ * the source manifold, 0 from the domain boundary), vartheta (angle label, rad), tau (s), host or
+ * device.  Synchronous.  For tests and diagnostics (the state otherwise stays on the device). */
 egb_status egb_read_state(egb_ctx *ctx, egb_solve_id solve, double *out);
 
 /* Copy the characteristic velocities: out = [6][n_theta][nz][nx] float32 holding Vx, Vz,

@@ -5,7 +5,7 @@ None of these routines shares arithmetic with the Eulerian oracle they check:
 * qP phase velocity of a VTI medium in Thomsen's parameters (exact formula, Tsvankin 1996), its
   group velocity V = v n + (dv/dtheta) n_theta by complex-step differentiation;
 * the 2-D Helmholtz Green's function (i/4) H0^(1)(k r) (scipy's Hankel function);
-* the steady-state labels of a homogeneous medium (straight rays from the source ball);
+* the steady-state labels of a homogeneous medium (straight rays from the source);
 * the geometrical-optics Green's function of a homogeneous anisotropic medium, from the stationary
   phase evaluation of its plane-wave (Fourier) representation.
 """
@@ -97,26 +97,20 @@ def homogeneous_go_green(x, z, xs, zs, omega, v_of, V_of, c_ref):
     return c_ref ** 2 * np.exp(1j * (omega * T + math.pi / 4)) / (v_of(th) * np.sqrt(8 * math.pi * omega * Jt)), T, th
 
 
-def homogeneous_labels(theta, X, Z, ghat, p, r0, extent):
+def homogeneous_labels(theta, X, Z, ghat, p, R_sigma):
     """Steady-state labels of a homogeneous medium with the source at the origin.
 
     theta: (nth,) phase angles; X, Z: node offsets from the source (nz, nx); ghat (nth, 2) unit
-    group directions; p (nth, 2) slownesses; r0 the ball radius; extent a distance beyond the grid.
-    A ray through (x, theta) is the straight line along ghat(theta).  If it left the ball, Y is
-    the point where it crossed the ball's surface (Y = x inside the ball); otherwise Y is pushed
-    back to `extent` along the ray (a boundary-origin ray).  Th = theta, tau = p(theta) . x.
+    group directions; p (nth, 2) slownesses; R_sigma the radius of the source manifold's disc.
+    A ray through (x, theta) is the straight line along ghat(theta): b = x x ghat (its distance from
+    the source at closest approach), Th = theta, tau = p(theta) . x, and q = 1 when it passed its
+    closest approach within R_sigma of the source (|b| <= R_sigma, x downstream of the foot point).
     """
     gx = ghat[:, 0][:, None, None]
     gz = ghat[:, 1][:, None, None]
     L = X[None] * gx + Z[None] * gz
     b = X[None] * gz - Z[None] * gx
-    r2 = X[None] ** 2 + Z[None] ** 2
-    inside = r2 <= r0 * r0
-    half = np.sqrt(np.maximum(r0 * r0 - b * b, 0.0))
-    from_ball = (np.abs(b) <= r0) & (L >= half)
-    s = np.where(inside, 0.0, np.where(from_ball, L - half, L + extent))
-    Yx = X[None] - s * gx
-    Yz = Z[None] - s * gz
+    q = ((np.abs(b) <= R_sigma) & (L >= 0)).astype(np.float64)
     tau = p[:, 0][:, None, None] * X[None] + p[:, 1][:, None, None] * Z[None]
     Th = np.broadcast_to(theta[:, None, None], tau.shape).copy()
-    return dict(Yx=Yx, Yz=Yz, Th=Th, tau=tau)
+    return dict(b=b, q=q, Th=Th, tau=tau)

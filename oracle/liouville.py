@@ -10,14 +10,24 @@ The paper marches in depth z, which limits it to rays with dz/dtau > 0 (Eq. 13).
 equations are taken in pseudo-time t on the full reduced phase space (x, z, theta), theta in [0, 2pi):
     d_t u + Vx d_x u + Vz d_z u + thetadot d_theta u = s_u,   s = 0 for labels, s = 1 for tau
 (with H normalised so that t is traveltime, the tau source p.V equals 1; Eq. 19's source is this one
-divided by dz/dt).  Labels: Yx, Yz (the position label of Eq. 20, two components, stored relative to
-the source x_s), Th (the angle label vartheta), tau.  The initial surface of Eq. 20 (the plane
-z = z_s) is replaced by a small ball B = {|x - x_s| <= r0} around the point source whose cells are
-frozen at the initial data
-    Y = x - x_s,  Th = theta,  tau = p_s(theta) . (x - x_s)
-(p_s the slowness of the medium at the source; exact in a locally homogeneous ball because p.V = 1).
-Two ghost layers in x and z hold the same initial data permanently (Dirichlet inflow); theta is
-periodic.  Angle-label differences are wrapped into [-pi, pi).
+divided by dz/dt).
+
+Labels: b, the impact parameter of the ray at the source (the full-angle counterpart of Eq. 20's
+position label X - x_s: Gamma = {b = 0} is Eq. 35's {X = x_s}); q, an indicator that the ray's
+labels come from the source manifold (1) rather than the domain boundary (0); Th, the angle label
+vartheta; tau.  Eq. 20's initial surface (the plane z = z_s) is replaced by the closest-approach
+manifold of the point source: every phase cell within R_Sigma of x_s whose ray is still approaching
+the source ((x - x_s) . g_s(theta) < 0, g_s the source medium's unit group direction), and every
+cell of a small ball |x - x_s| <= r0, is frozen at the
+straight-ray data of its own medium
+    b = (x - x_s) x g(x, theta),  q = 1,  Th = theta,  tau = p(x, theta) . (x - x_s)
+(g the unit group direction, p = n / v the slowness, 2-D cross product a x b = a_x b_z - a_z b_x).
+A ray leaves the frozen set where it passes closest to x_s, so downstream it carries the distance
+and phase angle of its closest approach, and tau its traveltime from the source when b = 0.  The
+source-manifold tube in phase space is then about 2 R_Sigma wide, so its edge (where q and b jump
+to boundary data) stays far from Gamma.  Two ghost layers in x and z hold the same straight-ray
+data (media clamped to the nearest node) with q = 0 (Dirichlet inflow); theta is periodic.
+Angle-label differences are wrapped into [-pi, pi).
 
 Discretisation: Jiang & Peng's third-order HJ-WENO in each of x, z, theta, upwinded by the sign of
 the velocity component; Shu & Osher's TVD-RK3; dt = cfl / max_cells(|Vx|/hx + |Vz|/hz +
@@ -32,7 +42,7 @@ import numpy as np
 from . import christoffel as _ch
 from . import medium as _md
 
-FIELDS = ('Yx', 'Yz', 'Th', 'tau')
+FIELDS = ('b', 'q', 'Th', 'tau')
 WENO_EPS_REL = 1e-6
 GHOST = 2
 
@@ -60,18 +70,26 @@ class Setup:
         self.ps = np.stack([np.sin(self.theta) / vs, np.cos(self.theta) / vs], axis=-1)
         self.c_ref = float(_ch.source_quantities(self.a_s, np.array([0.0]))[0][0])
         self.r0 = float(problem.ball_radius)
+        self.R_sigma = source_disc_radius(problem, self.r0)
         # node coordinates including the ghost layers
         ox, oz = problem.origin
         self.xg = ox + self.hx * np.arange(-GHOST, nx + GHOST)
         self.zg = oz + self.hz * np.arange(-GHOST, nz + GHOST)
-        dx = self.xg[GHOST:-GHOST] - self.xs[0]
-        dz = self.zg[GHOST:-GHOST] - self.xs[1]
-        self.ball = (dz[:, None] * dz[:, None] + dx[None, :] * dx[None, :]) <= self.r0 * self.r0
+        dx = (self.xg[GHOST:-GHOST] - self.xs[0])[None, None, :]
+        dz = (self.zg[GHOST:-GHOST] - self.xs[1])[None, :, None]
+        r2 = dz * dz + dx * dx
+        # approaching the source: (x - x_s) . g_s(theta) < 0 with the source medium's unit group
+        # direction (the disc is small enough that the local direction differs by a few degrees,
+        # which only moves the freeze point along rays with b != 0 by a second-order amount)
+        _, _, _, gs = _ch.source_quantities(self.a_s, self.theta)
+        self.gs = gs
+        dot = dx * gs[:, 0][:, None, None] + dz * gs[:, 1][:, None, None]
+        self.frozen = (r2 <= self.r0 * self.r0) | ((r2 <= self.R_sigma * self.R_sigma) & (dot < 0.0))
         rate = (np.abs(self.vel['Vx']) / self.hx + np.abs(self.vel['Vz']) / self.hz
                 + np.abs(self.vel['thetadot']) / self.dth)
         self.max_rate = float(rate.max())
         h = max(self.hx, self.hz)
-        self.eps = {'Yx': WENO_EPS_REL * h * h, 'Yz': WENO_EPS_REL * h * h,
+        self.eps = {'b': WENO_EPS_REL * h * h, 'q': WENO_EPS_REL,
                     'Th': WENO_EPS_REL * self.dth ** 2,
                     'tau': WENO_EPS_REL * (h / self.c_ref) ** 2}
 
@@ -79,17 +97,28 @@ class Setup:
         return cfl / self.max_rate
 
     def initial_state(self):
-        """Eq. 20 on the padded grid: Y = x - x_s, Th = theta, tau = p_s(theta) . (x - x_s)."""
+        """Straight-ray data of the local medium on every padded cell (media clamped at the
+        edges); q = 1 on the frozen source manifold, 0 elsewhere."""
+        pad = ((0, 0), (GHOST, GHOST), (GHOST, GHOST))
+        Vx = np.pad(self.vel['Vx'], pad, mode='edge')
+        Vz = np.pad(self.vel['Vz'], pad, mode='edge')
+        v = np.pad(self.vel['v'], pad, mode='edge')
+        Vn = np.hypot(Vx, Vz)
         X = (self.xg - self.xs[0])[None, None, :]
         Z = (self.zg - self.xs[1])[None, :, None]
-        shape = (self.nth, self.nz + 2 * GHOST, self.nx + 2 * GHOST)
-        st = {
-            'Yx': np.broadcast_to(X, shape).copy(),
-            'Yz': np.broadcast_to(Z, shape).copy(),
-            'Th': np.broadcast_to(self.theta[:, None, None], shape).copy(),
-            'tau': self.ps[:, 0][:, None, None] * X + self.ps[:, 1][:, None, None] * Z,
-        }
-        return st
+        th = self.theta[:, None, None]
+        b = X * (Vz / Vn) - Z * (Vx / Vn)
+        tau = (np.sin(th) * X + np.cos(th) * Z) / v
+        q = np.zeros_like(b)
+        q[:, GHOST:-GHOST, GHOST:-GHOST][self.frozen] = 1.0
+        return {'b': b, 'q': q, 'Th': np.broadcast_to(th, b.shape).copy(), 'tau': tau}
+
+
+def source_disc_radius(problem, r0):
+    """R_Sigma = max(4 r0, min(Lx, Lz) / 8): radius of the closest-approach manifold's disc."""
+    Lx = (problem.nx - 1) * problem.hx
+    Lz = (problem.nz - 1) * problem.hz
+    return max(4.0 * r0, min(Lx, Lz) / 8.0)
 
 
 def _weno3_pair(dm2, dm1, d0, dp1, eps):
@@ -141,7 +170,7 @@ def rhs(state, S):
         L = -(S.vel['Vx'] * ux + S.vel['Vz'] * uz + S.vel['thetadot'] * ut)
         if f == 'tau':
             L = L + 1.0
-        L[:, S.ball] = 0.0
+        L[S.frozen] = 0.0
         out[f] = L
     return out
 
@@ -152,13 +181,13 @@ def _interior(u, S):
 
 def rk3_step(state, S, dt):
     """Shu-Osher TVD-RK3: u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
-    u_new = 1/3 u + 2/3 (u2 + dt L(u2)).  Ghost layers and frozen ball cells keep their initial
-    data bit for bit (they are copied, not recombined)."""
+    u_new = 1/3 u + 2/3 (u2 + dt L(u2)).  Ghost layers and frozen cells keep their initial data bit
+    for bit (they are copied, not recombined)."""
     def combine(a, u, b, v, L):
         w = {f: state[f].copy() for f in FIELDS}
         for f in FIELDS:
             _interior(w[f], S)[...] = a * _interior(u[f], S) + b * (_interior(v[f], S) + dt * L[f])
-            _interior(w[f], S)[:, S.ball] = _interior(state[f], S)[:, S.ball]
+            _interior(w[f], S)[S.frozen] = _interior(state[f], S)[S.frozen]
         return w
     L0 = rhs(state, S)
     u1 = combine(0.0, state, 1.0, state, L0)
@@ -174,7 +203,7 @@ def _evolve_c(S, state, dt, steps):
     from .build import library
     lib = library()
     vel = [np.ascontiguousarray(S.vel[k], np.float64) for k in ('Vx', 'Vz', 'thetadot')]
-    ball = np.ascontiguousarray(S.ball, np.uint8)
+    ball = np.ascontiguousarray(S.frozen, np.uint8)
     eps = np.array([S.eps[f] for f in FIELDS], np.float64)
     fields = [np.ascontiguousarray(state[f], np.float64).copy() for f in FIELDS]
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)

@@ -3,7 +3,7 @@
  *
  * Same scheme, same order of operations as liouville.py (Eqs. 16, 19, 20 of the paper in pseudo-time):
  *   L(u) = -(Vx u_x + Vz u_z + thetadot u_theta) + s_u, s = 1 for tau, 0 for the labels,
- *   L = 0 on frozen source-ball cells; ghosts (2 layers in x and z) keep their initial data;
+ *   L = 0 on frozen cells (the source manifold); ghosts (2 layers in x, z) keep their initial data;
  *   theta periodic; differences of the angle label wrapped into [-pi, pi).
  *   Shu-Osher TVD-RK3.  Jiang-Peng third-order HJ-WENO, upwinded by the velocity sign.
  * Fields are padded arrays [nth][nz+4][nx+4] of doubles, x fastest.
@@ -42,7 +42,7 @@ typedef struct {
     int nth, nz, nx, pz, px; /* pz = nz + 4, px = nx + 4 */
     double hx, hz, dth;
     const double *Vx, *Vz, *Td; /* [nth][nz][nx] */
-    const unsigned char *ball;  /* [nz][nx] */
+    const unsigned char *ball;  /* [nth][nz][nx] frozen cells */
 } grid_t;
 
 static double derivative(const grid_t *g, const double *u, int k, int iz, int ix, int dim,
@@ -73,7 +73,7 @@ static void rhs(const grid_t *g, const double *u, double *L, double eps, int ang
         for (int iz = 0; iz < g->nz; ++iz)
             for (int ix = 0; ix < g->nx; ++ix) {
                 size_t c = ((size_t)k * g->nz + iz) * g->nx + ix;
-                if (g->ball[(size_t)iz * g->nx + ix]) { L[c] = 0.0; continue; }
+                if (g->ball[c]) { L[c] = 0.0; continue; }
                 double vx = g->Vx[c], vz = g->Vz[c], vt = g->Td[c];
                 double ux = derivative(g, u, k, iz, ix, 0, vx, eps, angle);
                 double uz = derivative(g, u, k, iz, ix, 1, vz, eps, angle);
@@ -82,7 +82,7 @@ static void rhs(const grid_t *g, const double *u, double *L, double eps, int ang
             }
 }
 
-/* w_interior = a * u + b * (v + dt * L); frozen ball cells copy u bit for bit */
+/* w_interior = a * u + b * (v + dt * L); frozen cells copy u bit for bit */
 static void combine(const grid_t *g, double *w, const double *u, const double *v, const double *L,
                     double a, double b, double dt) {
 #pragma omp parallel for schedule(static)
@@ -91,7 +91,7 @@ static void combine(const grid_t *g, double *w, const double *u, const double *v
             for (int ix = 0; ix < g->nx; ++ix) {
                 size_t c = ((size_t)k * g->nz + iz) * g->nx + ix;
                 size_t p = ((size_t)k * g->pz + iz + G) * g->px + ix + G;
-                if (g->ball[(size_t)iz * g->nx + ix]) { w[p] = u[p]; continue; }
+                if (g->ball[c]) { w[p] = u[p]; continue; }
                 w[p] = a * u[p] + b * (v[p] + dt * L[c]);
             }
 }
@@ -100,10 +100,10 @@ static void combine(const grid_t *g, double *w, const double *u, const double *v
 int oracle_rk3_steps(int nth, int nz, int nx, double hx, double hz, double dth,
                      const double *Vx, const double *Vz, const double *Td,
                      const unsigned char *ball, const double *eps, double dt, int steps,
-                     double *Yx, double *Yz, double *Th, double *tau) {
+                     double *b, double *q, double *Th, double *tau) {
     grid_t g = {nth, nz, nx, nz + 2 * G, nx + 2 * G, hx, hz, dth, Vx, Vz, Td, ball};
     size_t padded = (size_t)nth * g.pz * g.px, cells = (size_t)nth * nz * nx;
-    double *fields[4] = {Yx, Yz, Th, tau};
+    double *fields[4] = {b, q, Th, tau};
     double *u1 = malloc(padded * sizeof(double)), *u2 = malloc(padded * sizeof(double));
     double *L = malloc(cells * sizeof(double));
     if (!u1 || !u2 || !L) { free(u1); free(u2); free(L); return 1; }

@@ -7,10 +7,9 @@ dynamic ray tracing of Eq. 21 with the complex initial data of Eq. 24), amplitud
 
 Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only):
 
-* The ray through a phase cell (x, theta) carries the level-set labels (Y, vartheta, tau); its
-  impact parameter at the source is
-      b = (Y - x_s) x g_s(vartheta)          (2-D cross product a x b = a_x b_z - a_z b_x)
-  with g_s the unit group direction of the source medium, so Gamma = {b = 0} (Eq. 35).
+* The ray through a phase cell (x, theta) carries the level-set labels (b, q, vartheta, tau): b
+  its signed distance from x_s at closest approach (2-D cross product a x b = a_x b_z - a_z b_x),
+  q = 1 when those labels come from the source manifold, so Gamma = {b = 0} (Eq. 35).
 * Beam centres: for every theta and every grid row, each sign change of b between neighbouring
   ball-origin cells is one point of Gamma; everything there is interpolated linearly.  The beam is
   evaluated at the receivers of the same row with the horizontal offset (the paper's same-depth
@@ -33,10 +32,10 @@ Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only)
   the 2-D Helmholtz Green's function (i/4) H0^(1)(kr) as kr -> inf; the output is rho_s c_ref^2
   times the scalar qP Green's function (c_ref: source phase velocity along +z), phase exp(+i omega T)
   (Eq. 2).
-* Only rays that left the source ball count: a cell is ball-origin when |Y - x_s| <= r0 + 2h.
+* Only rays that carry source labels and have left the frozen manifold count (q > 1/2, not frozen).
 
 Arrivals (late arrivals included, Eq. 35): along theta at a node, every sign change of b between
-cells k and k+1 (sign(0) = +1) where both cells have |Y - x_s| <= r0 + 2h; T is tau interpolated
+cells k and k+1 (sign(0) = +1) where both cells are flagged; T is tau interpolated
 linearly at b = 0 and A the geometrical amplitude |u| sqrt(omega) of that ray,
       A = c_ref^2 sqrt(rho_s / rho_r) / (v_r sqrt(8 pi |V_s| |d_theta b|)),
 interpolated the same way.  Arrivals are sorted by T (then by angle index), at most kmax kept.
@@ -75,26 +74,18 @@ def _grad_theta(f, dth, wrap):
     return d / (2 * dth)
 
 
-def taper(dist, r0, h):
-    """1 for dist <= r0 + h, 0 for dist >= r0 + 3h, raised cosine in between."""
-    t = np.clip((dist - (r0 + h)) / (2 * h), 0.0, 1.0)
-    return 0.5 * (1.0 + np.cos(np.pi * t))
-
-
 def beam_fields(S, lab):
     """Frequency-independent per-cell quantities of the superposition (all float64)."""
-    Yx, Yz, Th, tau = lab['Yx'], lab['Yz'], lab['Th'], lab['tau']
-    vs, _, Vsn, ghat = _ch.source_quantities(S.a_s, Th)
-    b = Yx * ghat[..., 1] - Yz * ghat[..., 0]
-    h = max(S.hx, S.hz)
-    dist = np.sqrt(Yx * Yx + Yz * Yz)
+    b, q, Th, tau = lab['b'], lab['q'], lab['Th'], lab['tau']
+    vs, _, Vsn, _ = _ch.source_quantities(S.a_s, Th)
     return dict(
-        b=b, tau=tau, vs=vs, Vsn=Vsn, dist=dist, Th=Th,
+        b=b, tau=tau, vs=vs, Vsn=Vsn, Th=Th,
         bx=_grad_axis(b, S.hx, 2, False), bz=_grad_axis(b, S.hz, 1, False),
         bt=_grad_theta(b, S.dth, False),
         Tx=_grad_axis(Th, S.hx, 2, True), Tz=_grad_axis(Th, S.hz, 1, True),
         Tt=_grad_theta(Th, S.dth, True),
-        w=taper(dist, S.r0, h), flag=dist <= S.r0 + 2 * h,
+        # rays whose labels came from the source manifold and that have left it
+        flag=(q > 0.5) & ~S.frozen,
     )
 
 
@@ -280,3 +271,15 @@ def min_abs_b_at_crossings(S, lab):
     cross = flag & flagn & ((b >= 0) != (bn >= 0))
     m = np.where(cross, np.minimum(np.abs(b), np.abs(bn)), np.inf)
     return m.min(axis=0)
+
+
+def ambiguous_nodes(S, lab, b_tol, q_band=0.05):
+    """Nodes whose arrival count hinges on a decision below the rounding of an FP32 evaluation:
+    a sign change of b (between any two theta-neighbours) with min |b| < b_tol, or with a source
+    indicator q within q_band of the 1/2 threshold at either cell."""
+    b, q = lab['b'], lab['q']
+    bn, qn = np.roll(b, -1, axis=0), np.roll(q, -1, axis=0)
+    cross = (b >= 0) != (bn >= 0)
+    near_b = cross & (np.minimum(np.abs(b), np.abs(bn)) < b_tol)
+    near_q = cross & ((np.abs(q - 0.5) < q_band) | (np.abs(qn - 0.5) < q_band))
+    return (near_b | near_q).any(axis=0)

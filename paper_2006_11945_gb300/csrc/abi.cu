@@ -61,8 +61,8 @@ void free_solve(Solve *s) {
     cudaFree(s->velp64);
     cudaFree(s->vel);
     cudaFree(s->velp);
+    cudaFree(s->frozen);
     tma_release(*s);
-    cudaFree(s->ball);
     cudaFree(s->src);
     cudaFree(s->scratch);
     delete s;
@@ -257,7 +257,7 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     s->fp64 = c->opts.precision == EGB_FP64;
     size_t velp_b = (size_t)3 * g.field * (s->fp64 ? 8 : 4);
     size_t state64_b = (size_t)4 * g.field * 8;
-    s->bytes = (s->fp64 ? state_b + 3 * state64_b : 3 * state_b) + cells * 6 * 4 + velp_b + g.nz * 8 +
+    s->bytes = (s->fp64 ? state_b + 3 * state64_b : 3 * state_b) + cells * 6 * 4 + velp_b + cells +
                (24 + 4 * nth) * 4;
     if (s->bytes + (256u << 20) > free_bytes()) {
         delete s;
@@ -277,37 +277,30 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
         if (e == cudaSuccess) e = cudaMemsetAsync(s->velp, 0, velp_b, c->stream);
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 6 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&s->ball, g.nz * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&s->frozen, cells);
     if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_solve(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
     if (!s->fp64) {
         e = tma_prepare(*s);
         if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "tensor maps of the stencil"); }
     }
-    // frozen source ball: per row the ix range with (x - xs)^2 + (z - zs)^2 <= r0^2 (FP64)
-    std::vector<int2> ball(g.nz);
-    for (int iz = 0; iz < g.nz; ++iz) {
-        double dz = (g.oz + iz * g.hz) - s->zs;
-        int lo = g.nx, hi = -1;
-        for (int ix = 0; ix < g.nx; ++ix) {
-            double dx = (g.ox + ix * g.hx) - s->xs;
-            if (dz * dz + dx * dx <= s->r0 * s->r0) {
-                if (ix < lo) lo = ix;
-                hi = ix;
-            }
-        }
-        ball[iz] = make_int2(lo, hi);
+    // source manifold: ball radius r0 and disc radius R_Sigma = max(4 r0, min(Lx, Lz) / 8)
+    {
+        double Lx = (g.nx - 1) * g.hx, Lz = (g.nz - 1) * g.hz;
+        double L8 = (Lx < Lz ? Lx : Lz) / 8.0;
+        s->R_sigma = 4.0 * s->r0 > L8 ? 4.0 * s->r0 : L8;
     }
     float *d_rate = nullptr;
     e = cudaMalloc(&d_rate, 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_rate, 0, 4, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ball, ball.data(), g.nz * sizeof(int2), cudaMemcpyHostToDevice, c->stream);
     if (s->fp64) {
         if (e == cudaSuccess) e = launch_source_block(*s, c->stream);
         if (e == cudaSuccess) e = fp64_setup(*s, d_rate, c->stream);
     } else {
         if (e == cudaSuccess) e = launch_solve_setup(*s, c->d_err, d_rate, c->stream);
+        if (e == cudaSuccess) e = launch_frozen_mask(*s, c->stream);
         if (e == cudaSuccess) e = launch_init_state(*s, c->stream);
+        if (e == cudaSuccess) e = launch_zero_frozen_velocity(*s, c->stream);
     }
     float rate = 0, cref = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&rate, d_rate, 4, cudaMemcpyDeviceToHost, c->stream);

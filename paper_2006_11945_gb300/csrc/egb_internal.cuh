@@ -20,7 +20,8 @@ namespace egb {
 // holds depth index iz = r - 2 (two ghost rows on each side); column c holds ix = c - XPAD
 // (XPAD = 4 keeps the interior 16-byte aligned; columns XPAD-2, XPAD-1 and XPAD+nx, XPAD+nx+1 are
 // the ghost layers).  Ghosts hold the initial data permanently (Dirichlet inflow).
-// Fields: 0 Yx, 1 Yz (position label minus x_s), 2 vartheta, 3 tau_hi, 4 tau_lo (double-float tau).
+// Fields: 0 b (impact parameter at closest approach to the source), 1 q (source indicator),
+// 2 vartheta, 3 tau_hi, 4 tau_lo (double-float tau).
 // ---------------------------------------------------------------------------------------------
 constexpr int XPAD = 4;
 constexpr int ZPAD = 2;
@@ -50,6 +51,12 @@ __host__ __device__ constexpr int tri21(int I, int J) {
 __host__ __device__ constexpr int aidx(int i, int j, int k, int l) {
     return tri21(voigt(i, j), voigt(k, l));
 }
+
+// Source manifold.  A phase cell is frozen at its straight-ray data when it lies in the ball
+// |x - x_s| <= r0, or within R_Sigma of x_s while its ray still approaches the source
+// ((x - x_s) . g_s(theta) < 0, g_s the source medium's unit group direction).  The decision is
+// taken once per solve in FP64 (k_frozen) and stored as a byte mask; the stencil kernels see a
+// frozen cell as one whose stored velocity copy (velp) is exactly zero.
 
 // Double-float helpers (Knuth's TwoSum and Dekker's FastTwoSum).
 struct ff { float hi, lo; };
@@ -94,6 +101,8 @@ struct Solve {
     Medium *m;
     Grid2D g;
     double xs, zs, r0, w0;
+    double R_sigma;         // radius of the closest-approach manifold's disc
+    uint8_t *frozen = nullptr;  // [nth][nz][nx] 1 on the frozen source manifold
     std::vector<double> omega;
     float *state[3] = {nullptr, nullptr, nullptr};  // three padded buffers of NFIELD fields
     int cur = 0;                                     // buffer holding u^n
@@ -103,7 +112,6 @@ struct Solve {
     bool fp64 = false;      // plain all-FP64 form
     double *state64[3] = {nullptr, nullptr, nullptr};  // [4 fields] Yx, Yz, vartheta, tau (FP64 form)
     double *velp64 = nullptr;                           // [3] padded Vx, Vz, thetadot (FP64 form)
-    int2 *ball = nullptr;   // [nz] frozen ix range per row (lo > hi: none)
     float *src = nullptr;   // source block: a_s[21], rho_s, c_ref, then [nth] x (psx, psz)
     float *scratch = nullptr;  // superposition scratch (lazily sized)
     size_t scratch_bytes = 0;
@@ -134,7 +142,8 @@ cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const floa
                                unsigned *d_err, cudaStream_t s);
 cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, cudaStream_t s);
 cudaError_t launch_init_state(const Solve &sv, cudaStream_t s);
-cudaError_t launch_rk3_step(Solve &sv, float dt, cudaStream_t s);
+cudaError_t launch_frozen_mask(const Solve &sv, cudaStream_t s);
+cudaError_t launch_zero_frozen_velocity(const Solve &sv, cudaStream_t s);
 cudaError_t tma_prepare(Solve &sv);
 void tma_release(Solve &sv);
 size_t stage_desc_bytes();

@@ -107,14 +107,25 @@ __global__ void k_velocity64(int nx, int nz, int nth, const double *__restrict__
     }
 }
 
-__global__ void k_init64(Grid2D g, double xs, double zs, const double *__restrict__ ps, double *b0,
-                         double *b1, double *b2) {
+// Straight-ray data of the local medium on every padded cell (see the FP32 path).
+__global__ void k_init64(Grid2D g, double xs, double zs, const double *__restrict__ velp,
+                         const uint8_t *__restrict__ frozen, double *b0, double *b1, double *b2) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y, k = blockIdx.z;
     if (c >= g.pitch) return;
     int ix = c - XPAD, iz = r - ZPAD;
+    int cx = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
+    int cz = iz < 0 ? 0 : (iz >= g.nz ? g.nz - 1 : iz);
+    int64_t pc = pidx(g, k, cz, cx);
+    double vx = velp[pc], vz = velp[g.field + pc];
+    double th = 2.0 * M_PI * k / g.nth;
+    double s = sin(th), cth = cos(th);
+    double v = s * vx + cth * vz;  // n . V = v
     double x = g.ox + ix * g.hx - xs, z = g.oz + iz * g.hz - zs;
-    double vals[4] = {x, z, 2.0 * M_PI * k / g.nth, ps[2 * k] * x + ps[2 * k + 1] * z};
+    double vn = sqrt(vx * vx + vz * vz);
+    bool interior = ix >= 0 && ix < g.nx && iz >= 0 && iz < g.nz;
+    double q = (interior && frozen[cidx(g, k, iz, ix)]) ? 1.0 : 0.0;
+    double vals[4] = {(x * vz - z * vx) / vn, q, th, (s * x + cth * z) / v};
     int64_t o = (int64_t)k * g.plane + (int64_t)r * g.pitch + c;
     for (int f = 0; f < 4; ++f) {
         b0[f * g.field + o] = vals[f];
@@ -141,8 +152,7 @@ struct Stage64 {
     Grid2D g;
     const double *uk, *un;
     double *out;
-    const double *V;  // padded [3]: Vx, Vz, thetadot
-    const int2 *ball;
+    const double *V;  // padded [3]: Vx, Vz, thetadot (zero on frozen cells)
     double dt, coef, ihx, ihz, idth;
     double eps[4];
 };
@@ -154,12 +164,11 @@ __global__ void k_rk3_stage64(Stage64 A) {
     int k = blockIdx.z;
     if (ix >= g.nx || iz >= g.nz) return;
     int64_t p = pidx(g, k, iz, ix);
-    int2 br = A.ball[iz];
-    if (ix >= br.x && ix <= br.y) {
+    double vx = A.V[p], vz = A.V[g.field + p], vt = A.V[2 * g.field + p];
+    if (vx == 0.0 && vz == 0.0) {  // frozen cell of the source manifold
         for (int f = 0; f < 4; ++f) A.out[f * g.field + p] = A.un[f * g.field + p];
         return;
     }
-    double vx = A.V[p], vz = A.V[g.field + p], vt = A.V[2 * g.field + p];
     int kk[5] = {(k - 2 + g.nth) % g.nth, (k - 1 + g.nth) % g.nth, k, (k + 1) % g.nth, (k + 2) % g.nth};
     for (int f = 0; f < 4; ++f) {
         const double *u = A.uk + f * g.field;
@@ -226,8 +235,11 @@ cudaError_t fp64_setup(Solve &sv, float *d_rate, cudaStream_t s) {
         k_velocity64<<<(nodes + 127) / 128, 128, 0, s>>>(g.nx, g.nz, g.nth, a, dx, dz, g, sv.velp64, sv.vel,
                                                          d_rate);
         dim3 gi((g.pitch + 127) / 128, g.nz + 2 * ZPAD, g.nth);
-        k_init64<<<gi, 128, 0, s>>>(g, sv.xs, sv.zs, ps, sv.state64[0], sv.state64[1], sv.state64[2]);
-        e = cudaGetLastError();
+        e = launch_frozen_mask(sv, s);
+        k_init64<<<gi, 128, 0, s>>>(g, sv.xs, sv.zs, sv.velp64, sv.frozen, sv.state64[0], sv.state64[1],
+                                     sv.state64[2]);
+        if (e == cudaSuccess) e = launch_zero_frozen_velocity(sv, s);
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(a);
@@ -242,13 +254,13 @@ cudaError_t launch_rk3_step64(Solve &sv, double dt, cudaStream_t s) {
     Stage64 A;
     A.g = g;
     A.V = sv.velp64;
-    A.ball = sv.ball;
     A.dt = dt;
     A.ihx = 1.0 / g.hx;
     A.ihz = 1.0 / g.hz;
     A.idth = 1.0 / g.dth;
     double h = g.hx > g.hz ? g.hx : g.hz;
-    A.eps[0] = A.eps[1] = 1e-6 * h * h;
+    A.eps[0] = 1e-6 * h * h;  // impact parameter (m)
+    A.eps[1] = 1e-6;          // source indicator (dimensionless)
     A.eps[2] = 1e-6 * g.dth * g.dth;
     A.eps[3] = 1e-6 * (h / sv.c_ref) * (h / sv.c_ref);
     dim3 block(32, 4);

@@ -1,8 +1,10 @@
 // TMA-staged Liouville stencil (the hot loop): persistent, streaming along theta.
 //
 // Same scheme as the plain stage kernel (Eqs. 16, 19 in pseudo-time; third-order HJ-WENO upwinded
-// by the velocity sign; Shu-Osher TVD-RK3 in increment form; double-float tau; wrapped angle-label
-// differences; frozen ball copies u^n), organised for GB300:
+// by the velocity sign; Shu-Osher TVD-RK3 in increment form: u1 = u + dt L(u),
+// u2 = u + 1/4 ((u1 - u) + dt L(u1)), u_new = u + 2/3 ((u2 - u) + dt L(u2)); double-float tau kept
+// with an error-free sum; wrapped angle-label differences; frozen cells of the source manifold copy
+// u^n; ghosts are never written), organised for GB300:
 //
 //  * one CTA per SM loops over work items (x-tile of 64 cells, z-tile of 8 rows, theta chunk);
 //  * for each theta plane a single 4-D TMA copy brings all five state fields of the tile plus its
@@ -39,7 +41,6 @@ struct StageDesc {
     const CUtensorMap *mapN;  // interior map of u^n
     const CUtensorMap *mapV;  // interior map of the padded velocities
     float *out;
-    const int2 *ball;
     Grid2D g;
     float dt, coef, ihx, ihz, idth;
     float eps[4];
@@ -86,7 +87,8 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
 // ---- packed two-cell arithmetic ------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
+// a - b as one packed FMA (b * -1 + a is exactly the rounded difference)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -200,7 +202,6 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
         const int iz = z0 + tz;
         const int ixa = x0 + 2 * tx;
         const bool row_ok = iz < g.nz;
-        const int2 br = row_ok ? A.ball[iz] : make_int2(1, 0);
         for (int kk = 0; kk < kn; ++kk) {
             {
                 int s = (kk + 4) % RING;
@@ -285,8 +286,9 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
                     o[3] = f2(ra.hi, rb.hi);
                     o[4] = f2(ra.lo, rb.lo);
                 }
-                const bool fa = ixa >= br.x && ixa <= br.y;
-                const bool fb = ixa + 1 >= br.x && ixa + 1 <= br.y;
+                // frozen cells of the source manifold carry a zeroed velocity copy
+                const bool fa = vx.x == 0.f && vz.x == 0.f;
+                const bool fb = vx.y == 0.f && vz.y == 0.f;
                 const int64_t p = pidx(g, k, iz, ixa);
 #pragma unroll
                 for (int f = 0; f < NFIELD; ++f) {
@@ -412,13 +414,13 @@ static StageDesc make_desc(const Solve &sv, int stage, int r, int chunk) {
     const Grid2D &g = sv.g;
     StageDesc A;
     A.g = g;
-    A.ball = sv.ball;
     A.dt = (float)sv.dt;
     A.ihx = (float)(1.0 / g.hx);
     A.ihz = (float)(1.0 / g.hz);
     A.idth = (float)(1.0 / g.dth);
     double h = g.hx > g.hz ? g.hx : g.hz;
-    A.eps[0] = A.eps[1] = (float)(1e-6 * h * h);
+    A.eps[0] = (float)(1e-6 * h * h);  // impact parameter (m)
+    A.eps[1] = 1e-6f;                    // source indicator (dimensionless)
     A.eps[2] = (float)(1e-6 * g.dth * g.dth);
     A.eps[3] = (float)(1e-6 * (h / sv.c_ref) * (h / sv.c_ref));
     A.tiles_x = (g.nx + tma::TX - 1) / tma::TX;

@@ -3,8 +3,8 @@
 // Sec. 2, Eq. 5: a_ijkl = c_ijkl / rho (per node), with second-order central differences for its
 // gradient (second-order one-sided at the grid edges) and a 6x6 Cholesky positive-definiteness
 // check.  Eqs. 3-12: per phase cell the qP eigenpair and the ray velocities (christoffel.cuh).
-// Eq. 20 (generalised to a frozen source ball): labels Y = x - x_s, vartheta = theta,
-// tau = p_s(theta) . (x - x_s) on every cell, ghosts included.
+// Eq. 20 generalised to the closest-approach manifold of the point source: straight-ray labels
+// b = (x - x_s) x g, q, vartheta = theta, tau = p . (x - x_s) on every cell, ghosts included.
 #include "christoffel.cuh"
 
 namespace egb {
@@ -189,32 +189,106 @@ cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, 
 }
 
 // ------------------------------- initial level sets ---------------------------------------------
-__global__ void k_init(Grid2D g, double xs, double zs, const float *__restrict__ src, float *b0,
-                       float *b1, float *b2) {
+// Straight-ray data of the local medium (media clamped to the nearest node for ghosts):
+//   b = (x - x_s) x g,  q = 1 on the frozen source manifold else 0,  vartheta = theta,
+//   tau = p . (x - x_s) with p = n / v.
+__global__ void k_init(Grid2D g, double xs, double zs, const float *__restrict__ vel,
+                       const uint8_t *__restrict__ frozen, float *b0, float *b1, float *b2) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     int k = blockIdx.z;
     if (c >= g.pitch) return;
     int ix = c - XPAD, iz = r - ZPAD;
+    int cx = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
+    int cz = iz < 0 ? 0 : (iz >= g.nz ? g.nz - 1 : iz);
+    int64_t cells = (int64_t)g.nth * g.nx * g.nz;
+    int64_t o = cidx(g, k, cz, cx);
+    float vx = vel[o], vz = vel[cells + o], v = vel[3 * cells + o];
     double x = g.ox + ix * g.hx - xs;
     double z = g.oz + iz * g.hz - zs;
     double th = 2.0 * M_PI * k / g.nth;
-    double tau = (double)src[src_ps(k)] * x + (double)src[src_ps(k) + 1] * z;
+    double vn = sqrt((double)vx * vx + (double)vz * vz);
+    double bb = (x * vz - z * vx) / vn;
+    double tau = (sin(th) * x + cos(th) * z) / (double)v;
+    bool interior = ix >= 0 && ix < g.nx && iz >= 0 && iz < g.nz;
+    float q = (interior && frozen[cidx(g, k, iz, ix)]) ? 1.f : 0.f;
     float hi = (float)tau;
     float lo = (float)(tau - (double)hi);
-    float vals[NFIELD] = {(float)x, (float)z, (float)th, hi, lo};
-    int64_t o = (int64_t)k * g.plane + (int64_t)r * g.pitch + c;
+    float vals[NFIELD] = {(float)bb, q, (float)th, hi, lo};
+    int64_t p = (int64_t)k * g.plane + (int64_t)r * g.pitch + c;
 #pragma unroll
     for (int f = 0; f < NFIELD; ++f) {
-        b0[f * g.field + o] = vals[f];
-        b1[f * g.field + o] = vals[f];
-        b2[f * g.field + o] = vals[f];
+        b0[f * g.field + p] = vals[f];
+        b1[f * g.field + p] = vals[f];
+        b2[f * g.field + p] = vals[f];
     }
 }
 
 cudaError_t launch_init_state(const Solve &sv, cudaStream_t s) {
     dim3 grid((sv.g.pitch + 127) / 128, sv.g.nz + 2 * ZPAD, sv.g.nth);
-    k_init<<<grid, 128, 0, s>>>(sv.g, sv.xs, sv.zs, sv.src, sv.state[0], sv.state[1], sv.state[2]);
+    k_init<<<grid, 128, 0, s>>>(sv.g, sv.xs, sv.zs, sv.vel, sv.frozen, sv.state[0], sv.state[1], sv.state[2]);
+    return cudaGetLastError();
+}
+
+// ------------------------------- frozen source manifold (FP64, once per solve) ----------------------
+// Source-medium unit group direction g_s(theta_k) in double, a_s = c / rho interpolated bilinearly
+// from the medium's copy of the inputs (as the oracle does), then per cell
+//   frozen = r^2 <= r0^2 || (r^2 <= R_Sigma^2 && (x - x_s) . g_s < 0),  r = |x - x_s|,
+// with every product and sum rounded separately so the decision is reproducible.
+__global__ void k_frozen(Grid2D g, const float *__restrict__ c21, const float *__restrict__ rho, double xs,
+                         double zs, double r0, double R, uint8_t *__restrict__ frozen) {
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y, k = blockIdx.z;
+    __shared__ double gs[2];
+    if (threadIdx.x == 0) {
+        double fx = (xs - g.ox) / g.hx, fz = (zs - g.oz) / g.hz;
+        int jx = (int)floor(fx), jz = (int)floor(fz);
+        jx = jx < 0 ? 0 : (jx > g.nx - 2 ? g.nx - 2 : jx);
+        jz = jz < 0 ? 0 : (jz > g.nz - 2 ? g.nz - 2 : jz);
+        double tx = fx - jx, tz = fz - jz;
+        int n00 = jz * g.nx + jx;
+        int nn[4] = {n00, n00 + 1, n00 + g.nx, n00 + g.nx + 1};
+        double as[21];
+        for (int q = 0; q < 21; ++q) {
+            double f[4];
+            for (int m = 0; m < 4; ++m) f[m] = (double)c21[(int64_t)nn[m] * 21 + q] / (double)rho[nn[m]];
+            as[q] = (1 - tz) * ((1 - tx) * f[0] + tx * f[1]) + tz * ((1 - tx) * f[2] + tx * f[3]);
+        }
+        double th = 2.0 * M_PI * k / g.nth;
+        SrcVelT<double> r = source_velocity(as, sin(th), cos(th));
+        gs[0] = r.Vx / r.Vn;
+        gs[1] = r.Vz / r.Vn;
+    }
+    __syncthreads();
+    if (ix >= g.nx) return;
+    double dx = __dadd_rn(__dadd_rn(g.ox, __dmul_rn((double)ix, g.hx)), -xs);
+    double dz = __dadd_rn(__dadd_rn(g.oz, __dmul_rn((double)iz, g.hz)), -zs);
+    double r2 = __dadd_rn(__dmul_rn(dz, dz), __dmul_rn(dx, dx));
+    double dot = __dadd_rn(__dmul_rn(dx, gs[0]), __dmul_rn(dz, gs[1]));
+    bool f = r2 <= __dmul_rn(r0, r0) || (r2 <= __dmul_rn(R, R) && dot < 0.0);
+    frozen[cidx(g, k, iz, ix)] = f ? 1 : 0;
+}
+
+__global__ void k_zero_frozen(Grid2D g, const uint8_t *__restrict__ frozen, float *velp, double *velp64) {
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y, k = blockIdx.z;
+    if (ix >= g.nx || !frozen[cidx(g, k, iz, ix)]) return;
+    int64_t p = pidx(g, k, iz, ix);
+    for (int f = 0; f < 3; ++f) {
+        if (velp) velp[f * g.field + p] = 0.f;
+        if (velp64) velp64[f * g.field + p] = 0.0;
+    }
+}
+
+cudaError_t launch_frozen_mask(const Solve &sv, cudaStream_t s) {
+    dim3 grid((sv.g.nx + 127) / 128, sv.g.nz, sv.g.nth);
+    k_frozen<<<grid, 128, 0, s>>>(sv.g, sv.m->c21, sv.m->rho, sv.xs, sv.zs, sv.r0, sv.R_sigma, sv.frozen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_frozen_velocity(const Solve &sv, cudaStream_t s) {
+    dim3 grid((sv.g.nx + 127) / 128, sv.g.nz, sv.g.nth);
+    k_zero_frozen<<<grid, 128, 0, s>>>(sv.g, sv.frozen, sv.velp, sv.velp64);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,10 @@
 // Gaussian-beam superposition over the source manifold and arrival extraction.
 //
-// Sec. 5.  Gamma = {b = 0} (Eq. 35) with b = (Y - x_s) x g_s(vartheta) the impact parameter of the
-// ray at the source (g_s the unit group direction of the source medium, 2-D cross product
-// a x b = a_x b_z - a_z b_x); a cell counts as ball-origin when |Y - x_s| <= r0 + 2h.
+// Sec. 5.  Gamma = {b = 0} (Eq. 35) with b the label holding the ray's signed distance from x_s at
+// closest approach; a cell counts when its labels come from the source manifold (q > 1/2) and it
+// is not itself frozen.
 //
-//  k_beam_fields   per cell: b, ball-origin flag, |V_s(vartheta)|                     (Eq. 35)
+//  k_beam_fields   per cell: b, source flag, |V_s(vartheta)|                          (Eq. 35)
 //  k_centres       per grid line (row: fixed z, or column: fixed x) and angle: every sign change of
 //                  b between flagged neighbours is a beam centre; its level-set gradients give the
 //                  dynamic ray tracing (Eqs. 21-24) -> complex Hessian M (Eq. 25), spreading det C
@@ -33,7 +33,8 @@ struct SupArgs {
     float4 *rdat, *cdat;  // [n_omega][line slots]: E.re, E.im, M.re, M.im
     int n_omega;
     const double *omega_dev;
-    float w0, r0, flag_r2;
+    float w0;
+    const uint8_t *frozen;  // [cells] frozen source manifold
     float C1, C2, C3;     // 2 pi split for the range reduction
     unsigned *err;
 };
@@ -52,16 +53,15 @@ __global__ void k_beam_fields(SupArgs A) {
     int iz = blockIdx.y, k = blockIdx.z;
     if (ix >= g.nx) return;
     int64_t p = pidx(g, k, iz, ix);
-    float yx = A.st[p], yz = A.st[g.field + p], th = A.st[2 * g.field + p];
+    float b = A.st[p], q = A.st[g.field + p], th = A.st[2 * g.field + p];
     float s, c;
     sincosf(th, &s, &c);
     SrcVel r = source_velocity(as, s, c);
-    float inv = 1.f / r.Vn;
-    float b = yx * (r.Vz * inv) - yz * (r.Vx * inv);
     int64_t o = cidx(g, k, iz, ix);
     A.B[o] = b;
     A.VSN[o] = r.Vn;
-    A.FL[o] = (yx * yx + yz * yz) <= A.flag_r2 ? 1 : 0;
+    // rays that carry source labels and have left the frozen manifold
+    A.FL[o] = (q > 0.5f && !A.frozen[o]) ? 1 : 0;
 }
 
 // Gradient along x (dir 0) or z (dir 1) of a cell field F[cells], second order, one-sided at edges.
@@ -425,10 +425,7 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
     A.n_omega = (int)no;
     A.omega_dev = om;
     A.w0 = (float)sv.w0;
-    A.r0 = (float)sv.r0;
-    double h = g.hx > g.hz ? g.hx : g.hz;
-    double fr = sv.r0 + 2.0 * h;
-    A.flag_r2 = (float)(fr * fr);
+    A.frozen = sv.frozen;
     split_two_pi(A.C1, A.C2, A.C3);
     A.err = d_err;
     dim3 gb((g.nx + 127) / 128, g.nz, g.nth);

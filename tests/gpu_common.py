@@ -27,7 +27,7 @@ def run_oracle(problem, steps=None, kmax=8):
     lab = OL.interior_state(st, S)
     u = OS.green(S, lab, problem.omegas, problem.beam_width)
     cnt, T, A, over = OS.arrivals(S, lab, kmax)
-    amb = OS.min_abs_b_at_crossings(S, lab) < 1e-4 * max(problem.hx, problem.hz)
+    amb = OS.ambiguous_nodes(S, lab, 1e-4 * max(problem.hx, problem.hz))
     return dict(S=S, lab=lab, u=u, count=cnt, T=T, A=A, overflow=over, ambiguous=amb, dt=dt)
 
 

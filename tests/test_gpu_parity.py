@@ -2,9 +2,10 @@
 
 Tolerances (stated against the FP64 oracle): traveltime relative <= 1e-5, amplitude relative
 <= 1e-3, complex wavefield relative L2 <= 2e-3, arrival counts bit-exact at every node that is not
-ambiguous (oracle |b| < 1e-4 h at a crossing, where the sign of b is decided below the rounding of
-either side).  The level sets themselves are compared with bounds derived from FP32 rounding over
-the steps taken (labels: 2e-3 h; angle label: 2e-4 rad; tau: relative 1e-6).
+ambiguous (oracle |b| < 1e-4 h at a crossing, or a source indicator within 0.05 of its 1/2
+threshold there: decisions below the rounding of either side).  The level sets themselves are compared with bounds derived from FP32 rounding over
+the steps taken (impact parameter: 2e-3 h; source indicator: 2e-2, an indicator whose frozen-set boundary
+may be decided differently at rounding level; angle label: 2e-4 rad; tau: relative 1e-6).
 """
 import math
 
@@ -56,11 +57,12 @@ def test_state_parity(case):
     name, p, res, info, state, vel, ref = case
     lab = ref['lab']
     h = max(p.hx, p.hz)
-    ey = max(np.max(np.abs(state[0] - lab['Yx'])), np.max(np.abs(state[1] - lab['Yz']))) / h
+    ey = np.max(np.abs(state[0] - lab['b'])) / h
+    eq = np.max(np.abs(state[1] - lab['q']))
     et = np.max(np.abs(wrap(state[2] - lab['Th'])))
     etau = np.max(np.abs(state[3] - lab['tau'])) / np.max(np.abs(lab['tau']))
-    print(name, 'label err/h', ey, 'angle', et, 'tau rel', etau)
-    assert ey < 2e-3 and et < 2e-4 and etau < 1e-6, (name, ey, et, etau)
+    print(name, 'b err/h', ey, 'q', eq, 'angle', et, 'tau rel', etau)
+    assert ey < 2e-3 and eq < 2e-2 and et < 2e-4 and etau < 1e-6, (name, ey, eq, et, etau)
 
 
 def test_output_parity(case):

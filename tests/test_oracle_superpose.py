@@ -27,7 +27,7 @@ def _exact_setup(problem):
     Z, X = np.meshgrid(z, x, indexing='ij')
     v, V, Vn, g = CH.source_quantities(S.a_s, S.theta)
     p = np.stack([np.sin(S.theta) / v, np.cos(S.theta) / v], -1)
-    lab = CF.homogeneous_labels(S.theta, X, Z, g, p, S.r0, 1e4)
+    lab = CF.homogeneous_labels(S.theta, X, Z, g, p, S.R_sigma)
     edge = np.minimum(np.minimum(X - X.min(), X.max() - X), np.minimum(Z - Z.min(), Z.max() - Z))
     return S, lab, X, Z, edge
 
