@@ -54,14 +54,15 @@ def _wrap(d):
 class Setup:
     """Everything the evolution needs for one 2-D problem (float64)."""
 
-    def __init__(self, problem):
+    def __init__(self, problem, vel=None):
         self.p = problem
         nx, nz, nth = problem.nx, problem.nz, problem.n_theta
         self.nx, self.nz, self.nth = nx, nz, nth
         self.hx, self.hz = float(problem.hx), float(problem.hz)
         self.dth = 2.0 * math.pi / nth
         self.a, self.da_dx, self.da_dz, self.rho = _md.medium_2d(problem)
-        self.vel = _ch.velocity_field_2d(self.a, self.da_dx, self.da_dz, nth)
+        # vel: the same fields computed beforehand (e.g. by velocity_field_pooled)
+        self.vel = _ch.velocity_field_2d(self.a, self.da_dx, self.da_dz, nth) if vel is None else vel
         self.xs = np.array(problem.xs, np.float64)
         self.a_s = _md.bilinear_at(self.a, problem, self.xs[0], self.xs[1])
         self.rho_s = float(_md.bilinear_at(self.rho, problem, self.xs[0], self.xs[1]))
@@ -112,6 +113,26 @@ class Setup:
         q = np.zeros_like(b)
         q[:, GHOST:-GHOST, GHOST:-GHOST][self.frozen] = 1.0
         return {'b': b, 'q': q, 'Th': np.broadcast_to(th, b.shape).copy(), 'tau': tau}
+
+
+def _velocity_planes(args):
+    problem, ks = args
+    a, da_dx, da_dz, _ = _md.medium_2d(problem)
+    return ks, _ch.velocity_field_2d(a, da_dx, da_dz, problem.n_theta, ks)
+
+
+def velocity_field_pooled(problem, processes=8):
+    """velocity_field_2d of the problem's medium, its angle planes split over a pool of `processes`
+    spawned worker processes (for large grids; the planes are computed exactly as in one process)."""
+    import multiprocessing as mp
+    nth = problem.n_theta
+    parts = [list(range(i, nth, processes)) for i in range(processes) if i < nth]
+    out = {k: np.empty((nth, problem.nz, problem.nx)) for k in ('Vx', 'Vz', 'thetadot', 'v', 'pdx', 'pdz')}
+    with mp.get_context('spawn').Pool(len(parts)) as pool:
+        for ks, vel in pool.imap_unordered(_velocity_planes, [(problem, ks) for ks in parts]):
+            for key in out:
+                out[key][ks] = vel[key]
+    return out
 
 
 def source_disc_radius(problem, r0):

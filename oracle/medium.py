@@ -59,3 +59,32 @@ def bilinear_at(field, problem, x, z):
     tz = fz - iz
     return ((1 - tz) * ((1 - tx) * field[iz, ix] + tx * field[iz, ix + 1])
             + tz * ((1 - tx) * field[iz + 1, ix] + tx * field[iz + 1, ix + 1]))
+
+
+def medium_3d(problem):
+    """a (nz, ny, nx, 3,3,3,3), da/dx, da/dy, da/dz (same shape), rho (nz, ny, nx) for a 3-D problem
+    (second-order central differences, second-order one-sided at the edges)."""
+    nz, ny, nx = problem.nz, problem.ny, problem.nx
+    c21 = np.asarray(problem.c21, np.float64).reshape(nz, ny, nx, 21)
+    rho = np.asarray(problem.rho, np.float64).reshape(nz, ny, nx)
+    a = density_normalised(c21, rho)
+    da_dz = np.gradient(a, problem.hz, axis=0, edge_order=2)
+    da_dy = np.gradient(a, problem.hy, axis=1, edge_order=2)
+    da_dx = np.gradient(a, problem.hx, axis=2, edge_order=2)
+    return a, da_dx, da_dy, da_dz, rho
+
+
+def trilinear_at(field, problem, x, y, z):
+    """Trilinear interpolation of a node field (nz, ny, nx, ...) at the point (x, y, z)."""
+    o = problem.origin
+    f = [(x - o[0]) / problem.hx, (y - o[1]) / problem.hy, (z - o[2]) / problem.hz]
+    n = [problem.nx, problem.ny, problem.nz]
+    i = [int(np.clip(np.floor(f[d]), 0, n[d] - 2)) for d in range(3)]
+    t = [f[d] - i[d] for d in range(3)]
+    out = 0.0
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                w = ((t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2]))
+                out = out + w * field[i[2] + dz, i[1] + dy, i[0] + dx]
+    return out

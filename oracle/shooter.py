@@ -110,8 +110,11 @@ def shoot(problem, n_rays=2048, dt=None, t_max=None):
                 exit_time=exit_time, medium=M, a_s=a_s)
 
 
-def arrivals(problem, fan, min_dist=0.0):
-    """Ray-tube arrivals at the grid nodes: count, sorted times and GO amplitudes per node."""
+def arrivals(problem, fan, min_dist=0.0, node_mask=None):
+    """Ray-tube arrivals at the grid nodes: count, sorted times and GO amplitudes per node.
+
+    node_mask (nz, nx) bool, optional: collect arrivals only at these nodes (the others report 0),
+    which bounds the work on large grids; the arrivals of a node do not depend on the others."""
     X, Z, T = fan['X'], fan['Z'], fan['T']
     M = fan['medium']
     nx, nz = problem.nx, problem.nz
@@ -155,9 +158,11 @@ def arrivals(problem, fan, min_dist=0.0):
                 with np.errstate(divide='ignore', invalid='ignore'):
                     l1 = ((Bz - Cz) * (px - Cx) + (Cx - Bx) * (pz - Cz)) / den
                     l2 = ((Cz - Az) * (px - Cx) + (Ax - Cx) * (pz - Cz)) / den
-                l3 = 1 - l1 - l2
+                    l3 = 1 - l1 - l2
                 # half-open inclusion so a node on a shared edge is counted once
                 inside = ok & (den != 0) & (l1 >= 0) & (l2 >= 0) & (l3 > 0)
+                if node_mask is not None:
+                    inside[inside] = node_mask[iz[inside], ix[inside]]
                 for q in np.nonzero(inside)[0]:
                     key = (int(iz[q]), int(ix[q]))
                     tt = l1[q] * ta[q] + l2[q] * tb[q] + l3[q] * tc[q]

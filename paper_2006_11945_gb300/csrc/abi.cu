@@ -62,6 +62,7 @@ void free_solve(Solve *s) {
     cudaFree(s->vel);
     cudaFree(s->velp);
     cudaFree(s->frozen);
+    cudaFree(s->gs64);
     tma_release(*s);
     cudaFree(s->src);
     cudaFree(s->scratch);
@@ -278,6 +279,7 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 6 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->frozen, cells);
+    if (e == cudaSuccess) e = cudaMalloc(&s->gs64, sizeof(double) * 2 * s->g.nth);
     if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_solve(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
     if (!s->fp64) {
@@ -316,8 +318,15 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
         egb_status st = ensure_desc(c, 1);
         if (st != EGB_OK) { free_solve(s); return st; }
         s->dt = 0.5 / s->max_rate;
-        e = tma_autotune(*s, c->d_desc, c->d_err, c->stream);
-        if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "stencil autotuning"); }
+        uint64_t shape = ((uint64_t)s->g.nx << 40) ^ ((uint64_t)s->g.nz << 20) ^ (uint64_t)s->g.nth;
+        auto it = c->tuned_chunk.find(shape);
+        if (it != c->tuned_chunk.end()) {
+            tma_set_chunk(*s, it->second);
+        } else {
+            e = tma_autotune(*s, c->d_desc, c->d_err, c->stream);
+            if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "stencil autotuning"); }
+            c->tuned_chunk[shape] = tma_chunk(*s);
+        }
     }
     uint64_t id = c->next_id++;
     c->solves[id] = s;

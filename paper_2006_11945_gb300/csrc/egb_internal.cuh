@@ -103,6 +103,7 @@ struct Solve {
     double xs, zs, r0, w0;
     double R_sigma;         // radius of the closest-approach manifold's disc
     uint8_t *frozen = nullptr;  // [nth][nz][nx] 1 on the frozen source manifold
+    double *gs64 = nullptr;     // [nth][2] source-medium unit group direction (FP64)
     std::vector<double> omega;
     float *state[3] = {nullptr, nullptr, nullptr};  // three padded buffers of NFIELD fields
     int cur = 0;                                     // buffer holding u^n
@@ -135,6 +136,9 @@ struct Ctx {
     StageDesc *d_desc = nullptr;  // stage descriptors of batched launches (device)
     int desc_cap = 0;             // capacity in solves (9 descriptors per solve)
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
+    // theta chunk chosen by the stencil autotuner, per grid shape (nx, nz, n_theta): later solves
+    // of the same shape reuse it instead of timing the candidates again
+    std::unordered_map<uint64_t, int> tuned_chunk;
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -148,6 +152,7 @@ cudaError_t tma_prepare(Solve &sv);
 void tma_release(Solve &sv);
 size_t stage_desc_bytes();
 int tma_chunk(const Solve &sv);
+void tma_set_chunk(Solve &sv, int chunk);
 cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s);
 cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
                          cudaStream_t cap);

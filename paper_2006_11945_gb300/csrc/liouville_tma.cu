@@ -448,6 +448,10 @@ static void launch_stage(int stage, const StageDesc *d, int nsolves, int total, 
 
 int tma_chunk(const Solve &sv) { return sv.tma ? ((TmaMaps *)sv.tma)->chunk : 0; }
 
+void tma_set_chunk(Solve &sv, int chunk) {
+    if (sv.tma) ((TmaMaps *)sv.tma)->chunk = chunk;
+}
+
 // Autotuner: time stage 1 (reads u^n, writes a stage buffer, so the state is untouched) for each
 // theta-chunk candidate and keep the fastest.  Synchronises the stream.
 cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s) {

@@ -48,27 +48,31 @@ __global__ void k_medium_a(int nodes, const float *__restrict__ c21, const float
     if (!ok) atomicOr(err, DeviceErrors::NOT_PD);
 }
 
-__global__ void k_medium_grad(int nx, int nz, float ihx, float ihz, const float *__restrict__ a,
-                              float *__restrict__ dadx, float *__restrict__ dadz) {
+// Gradient of a = c / rho from the float inputs, evaluated in FP64 and rounded once: on fine grids
+// the neighbour differences of FP32-rounded a would carry a relative error 2^-24 |a| / (h |grad a|).
+__device__ __forceinline__ double a_at(const float *__restrict__ c21, const float *__restrict__ rho,
+                                       int64_t node, int q) {
+    return (double)c21[node * 21 + q] / (double)rho[node];
+}
+
+__global__ void k_medium_grad(int nx, int nz, double ihx, double ihz, const float *__restrict__ c21,
+                              const float *__restrict__ rho, float *__restrict__ dadx,
+                              float *__restrict__ dadz) {
     int ix = blockIdx.x * blockDim.x + threadIdx.x;
     int iz = blockIdx.y;
     int q = blockIdx.z;
     if (ix >= nx) return;
-    const float *f = a + (int64_t)q * nx * nz + (int64_t)iz * nx;
-    float gx;
-    if (ix == 0) gx = (4.f * (f[1] - f[0]) - (f[2] - f[0])) * 0.5f * ihx;
-    else if (ix == nx - 1) gx = (4.f * (f[nx - 1] - f[nx - 2]) - (f[nx - 1] - f[nx - 3])) * 0.5f * ihx;
-    else gx = (f[ix + 1] - f[ix - 1]) * 0.5f * ihx;
-    const float *col = a + (int64_t)q * nx * nz + ix;
-    float gz;
-    if (iz == 0) gz = (4.f * (col[nx] - col[0]) - (col[2 * nx] - col[0])) * 0.5f * ihz;
-    else if (iz == nz - 1)
-        gz = (4.f * (col[(int64_t)(nz - 1) * nx] - col[(int64_t)(nz - 2) * nx]) -
-              (col[(int64_t)(nz - 1) * nx] - col[(int64_t)(nz - 3) * nx])) * 0.5f * ihz;
-    else gz = (col[(int64_t)(iz + 1) * nx] - col[(int64_t)(iz - 1) * nx]) * 0.5f * ihz;
+    auto A = [&](int jx, int jz) { return a_at(c21, rho, (int64_t)jz * nx + jx, q); };
+    double gx, gz;
+    if (ix == 0) gx = (4.0 * (A(1, iz) - A(0, iz)) - (A(2, iz) - A(0, iz))) * 0.5 * ihx;
+    else if (ix == nx - 1) gx = (4.0 * (A(nx - 1, iz) - A(nx - 2, iz)) - (A(nx - 1, iz) - A(nx - 3, iz))) * 0.5 * ihx;
+    else gx = (A(ix + 1, iz) - A(ix - 1, iz)) * 0.5 * ihx;
+    if (iz == 0) gz = (4.0 * (A(ix, 1) - A(ix, 0)) - (A(ix, 2) - A(ix, 0))) * 0.5 * ihz;
+    else if (iz == nz - 1) gz = (4.0 * (A(ix, nz - 1) - A(ix, nz - 2)) - (A(ix, nz - 1) - A(ix, nz - 3))) * 0.5 * ihz;
+    else gz = (A(ix, iz + 1) - A(ix, iz - 1)) * 0.5 * ihz;
     int64_t o = (int64_t)q * nx * nz + (int64_t)iz * nx + ix;
-    dadx[o] = gx;
-    dadz[o] = gz;
+    dadx[o] = (float)gx;
+    dadz[o] = (float)gz;
 }
 
 cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const float *rho_dev,
@@ -76,8 +80,8 @@ cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const floa
     int nodes = m.nx * m.nz;
     k_medium_a<<<(nodes + 127) / 128, 128, 0, s>>>(nodes, c21_dev, rho_dev, m.a, d_err);
     dim3 grid((m.nx + 127) / 128, m.nz, 21);
-    k_medium_grad<<<grid, 128, 0, s>>>(m.nx, m.nz, (float)(1.0 / m.hx), (float)(1.0 / m.hz), m.a,
-                                       m.dadx, m.dadz);
+    k_medium_grad<<<grid, 128, 0, s>>>(m.nx, m.nz, 1.0 / m.hx, 1.0 / m.hz, c21_dev, rho_dev, m.dadx,
+                                       m.dadz);
     cudaMemcpyAsync(m.rho, rho_dev, sizeof(float) * nodes, cudaMemcpyDeviceToDevice, s);
     return cudaGetLastError();
 }
@@ -197,6 +201,13 @@ __global__ void k_init(Grid2D g, double xs, double zs, const float *__restrict__
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     int k = blockIdx.z;
+    __shared__ double sc[2];  // sin, cos of theta_k (one angle per block)
+    if (threadIdx.x == 0) {
+        double th = 2.0 * M_PI * k / g.nth;
+        sc[0] = sin(th);
+        sc[1] = cos(th);
+    }
+    __syncthreads();
     if (c >= g.pitch) return;
     int ix = c - XPAD, iz = r - ZPAD;
     int cx = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
@@ -209,7 +220,7 @@ __global__ void k_init(Grid2D g, double xs, double zs, const float *__restrict__
     double th = 2.0 * M_PI * k / g.nth;
     double vn = sqrt((double)vx * vx + (double)vz * vz);
     double bb = (x * vz - z * vx) / vn;
-    double tau = (sin(th) * x + cos(th) * z) / (double)v;
+    double tau = (sc[0] * x + sc[1] * z) / (double)v;
     bool interior = ix >= 0 && ix < g.nx && iz >= 0 && iz < g.nz;
     float q = (interior && frozen[cidx(g, k, iz, ix)]) ? 1.f : 0.f;
     float hi = (float)tau;
@@ -232,39 +243,42 @@ cudaError_t launch_init_state(const Solve &sv, cudaStream_t s) {
 
 // ------------------------------- frozen source manifold (FP64, once per solve) ----------------------
 // Source-medium unit group direction g_s(theta_k) in double, a_s = c / rho interpolated bilinearly
-// from the medium's copy of the inputs (as the oracle does), then per cell
-//   frozen = r^2 <= r0^2 || (r^2 <= R_Sigma^2 && (x - x_s) . g_s < 0),  r = |x - x_s|,
+// from the medium's copy of the inputs (as the oracle does): one thread per angle.
+__global__ void k_source_dirs(Grid2D g, const float *__restrict__ c21, const float *__restrict__ rho,
+                              double xs, double zs, double *__restrict__ gs) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nth) return;
+    double fx = (xs - g.ox) / g.hx, fz = (zs - g.oz) / g.hz;
+    int jx = (int)floor(fx), jz = (int)floor(fz);
+    jx = jx < 0 ? 0 : (jx > g.nx - 2 ? g.nx - 2 : jx);
+    jz = jz < 0 ? 0 : (jz > g.nz - 2 ? g.nz - 2 : jz);
+    double tx = fx - jx, tz = fz - jz;
+    int n00 = jz * g.nx + jx;
+    int nn[4] = {n00, n00 + 1, n00 + g.nx, n00 + g.nx + 1};
+    double as[21];
+    for (int q = 0; q < 21; ++q) {
+        double f[4];
+        for (int m = 0; m < 4; ++m) f[m] = (double)c21[(int64_t)nn[m] * 21 + q] / (double)rho[nn[m]];
+        as[q] = (1 - tz) * ((1 - tx) * f[0] + tx * f[1]) + tz * ((1 - tx) * f[2] + tx * f[3]);
+    }
+    double th = 2.0 * M_PI * k / g.nth;
+    SrcVelT<double> r = source_velocity(as, sin(th), cos(th));
+    gs[2 * k] = r.Vx / r.Vn;
+    gs[2 * k + 1] = r.Vz / r.Vn;
+}
+
+// Per cell: frozen = r^2 <= r0^2 || (r^2 <= R_Sigma^2 && (x - x_s) . g_s(theta_k) < 0), r = |x - x_s|,
 // with every product and sum rounded separately so the decision is reproducible.
-__global__ void k_frozen(Grid2D g, const float *__restrict__ c21, const float *__restrict__ rho, double xs,
-                         double zs, double r0, double R, uint8_t *__restrict__ frozen) {
+__global__ void k_frozen(Grid2D g, const double *__restrict__ gsd, double xs, double zs, double r0, double R,
+                         uint8_t *__restrict__ frozen) {
     int ix = blockIdx.x * blockDim.x + threadIdx.x;
     int iz = blockIdx.y, k = blockIdx.z;
-    __shared__ double gs[2];
-    if (threadIdx.x == 0) {
-        double fx = (xs - g.ox) / g.hx, fz = (zs - g.oz) / g.hz;
-        int jx = (int)floor(fx), jz = (int)floor(fz);
-        jx = jx < 0 ? 0 : (jx > g.nx - 2 ? g.nx - 2 : jx);
-        jz = jz < 0 ? 0 : (jz > g.nz - 2 ? g.nz - 2 : jz);
-        double tx = fx - jx, tz = fz - jz;
-        int n00 = jz * g.nx + jx;
-        int nn[4] = {n00, n00 + 1, n00 + g.nx, n00 + g.nx + 1};
-        double as[21];
-        for (int q = 0; q < 21; ++q) {
-            double f[4];
-            for (int m = 0; m < 4; ++m) f[m] = (double)c21[(int64_t)nn[m] * 21 + q] / (double)rho[nn[m]];
-            as[q] = (1 - tz) * ((1 - tx) * f[0] + tx * f[1]) + tz * ((1 - tx) * f[2] + tx * f[3]);
-        }
-        double th = 2.0 * M_PI * k / g.nth;
-        SrcVelT<double> r = source_velocity(as, sin(th), cos(th));
-        gs[0] = r.Vx / r.Vn;
-        gs[1] = r.Vz / r.Vn;
-    }
-    __syncthreads();
     if (ix >= g.nx) return;
+    double gx = gsd[2 * k], gz = gsd[2 * k + 1];
     double dx = __dadd_rn(__dadd_rn(g.ox, __dmul_rn((double)ix, g.hx)), -xs);
     double dz = __dadd_rn(__dadd_rn(g.oz, __dmul_rn((double)iz, g.hz)), -zs);
     double r2 = __dadd_rn(__dmul_rn(dz, dz), __dmul_rn(dx, dx));
-    double dot = __dadd_rn(__dmul_rn(dx, gs[0]), __dmul_rn(dz, gs[1]));
+    double dot = __dadd_rn(__dmul_rn(dx, gx), __dmul_rn(dz, gz));
     bool f = r2 <= __dmul_rn(r0, r0) || (r2 <= __dmul_rn(R, R) && dot < 0.0);
     frozen[cidx(g, k, iz, ix)] = f ? 1 : 0;
 }
@@ -281,8 +295,9 @@ __global__ void k_zero_frozen(Grid2D g, const uint8_t *__restrict__ frozen, floa
 }
 
 cudaError_t launch_frozen_mask(const Solve &sv, cudaStream_t s) {
+    k_source_dirs<<<(sv.g.nth + 127) / 128, 128, 0, s>>>(sv.g, sv.m->c21, sv.m->rho, sv.xs, sv.zs, sv.gs64);
     dim3 grid((sv.g.nx + 127) / 128, sv.g.nz, sv.g.nth);
-    k_frozen<<<grid, 128, 0, s>>>(sv.g, sv.m->c21, sv.m->rho, sv.xs, sv.zs, sv.r0, sv.R_sigma, sv.frozen);
+    k_frozen<<<grid, 128, 0, s>>>(sv.g, sv.gs64, sv.xs, sv.zs, sv.r0, sv.R_sigma, sv.frozen);
     return cudaGetLastError();
 }
 

@@ -291,3 +291,119 @@ def request_stream(rate=200.0, duration=60.0, seed=4, max_requests=None):
         if max_requests is not None and len(reqs) >= max_requests:
             break
     return reqs
+
+
+# ---------------------------------------------------------------------------------------------
+# 3-D workloads.  Grids are stored z-major, then y, with x fastest (node = (iz*ny + iy)*nx + ix).
+# Phase directions n = (sin th cos ph, sin th sin ph, cos th): n_theta polar samples at cell
+# centres th_j = (j + 1/2) pi / n_theta, n_phi azimuth samples ph_k = 2 pi k / n_phi (n_phi even).
+
+@dataclass
+class Problem3D:
+    """One 3-D solve request: medium on an nz x ny x nx node grid plus the source description."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    hx: float
+    hy: float
+    hz: float
+    c21: np.ndarray                  # (nz*ny*nx, 21) float32, Pa
+    rho: np.ndarray                  # (nz*ny*nx,) float32, kg/m^3
+    xs: Tuple[float, float, float]   # source (x, y, z), m
+    n_theta: int                     # polar samples (cell centred)
+    n_phi: int                       # azimuth samples (even)
+    freqs: List[float]
+    beam_width: float
+    steps: int
+    cfl: float = 0.5
+    r0: Optional[float] = None
+    origin: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def omegas(self):
+        return [2.0 * math.pi * f for f in self.freqs]
+
+    @property
+    def ball_radius(self):
+        return self.r0 if self.r0 is not None else 2.0 * max(self.hx, self.hy, self.hz)
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz * self.n_theta * self.n_phi
+
+
+def default_steps_3d(n, h, vp=3000.0):
+    """ceil(1.1 T / dt) for a cube of n nodes at spacing h with the source at the centre: T = the
+    half diagonal over 0.9 vp (slowest qP speed of a +-10 % medium), dt = 0.5 h / (sqrt(3) 1.1 vp)
+    (CFL 0.5 with every group-velocity component at its bound).  387 steps at 96^3, 10 m."""
+    t_exit = math.sqrt(3.0) * 0.5 * n * h / (0.9 * vp)
+    dt = 0.5 * h / (math.sqrt(3.0) * 1.1 * vp)
+    return int(math.ceil(1.1 * t_exit / dt))
+
+
+def _cube(C, rho, n):
+    C = np.broadcast_to(C, (n, n, n, 6, 6))
+    return _pack(C, np.broadcast_to(np.asarray(rho, np.float64), (n, n, n)))
+
+
+def isotropic_homogeneous_3d(n=32, h=10.0, n_theta=12, n_phi=24, steps=None, vp=3000.0, vs=1700.0,
+                             rho=2300.0, freqs=(15.0,), beam_width=50.0, cfl=0.5):
+    """Homogeneous isotropic cube, source at the centre node."""
+    mu = rho * vs ** 2
+    lam = rho * vp ** 2 - 2 * mu
+    c21, r = _cube(isotropic_voigt(lam, mu), rho, n)
+    xs = ((n // 2) * h,) * 3
+    steps = default_steps_3d(n, h, vp) if steps is None else steps
+    return Problem3D('isotropic_homogeneous_3d', n, n, n, h, h, h, c21, r, xs, n_theta, n_phi,
+                     list(freqs), beam_width, steps, cfl, meta=dict(vp=vp, vs=vs, rho=rho))
+
+
+def vti_homogeneous_3d(n=32, h=10.0, n_theta=12, n_phi=24, steps=None, vp0=3000.0, vs0=1500.0,
+                       eps=0.20, delta=0.10, rho=2200.0, freqs=(15.0,), beam_width=50.0, cfl=0.5):
+    """Homogeneous VTI cube (Thomsen parameters), source at the centre node."""
+    c21, r = _cube(thomsen_vti_voigt(vp0, vs0, eps, delta, rho), rho, n)
+    xs = ((n // 2) * h,) * 3
+    steps = default_steps_3d(n, h, vp0) if steps is None else steps
+    return Problem3D('vti_homogeneous_3d', n, n, n, h, h, h, c21, r, xs, n_theta, n_phi,
+                     list(freqs), beam_width, steps, cfl,
+                     meta=dict(vp0=vp0, vs0=vs0, eps=eps, delta=delta, rho=rho))
+
+
+def triclinic_3d(n=96, h=10.0, n_theta=24, n_phi=48, steps=None, freqs=(15.0,), beam_width=50.0,
+                 seed=5, cfl=0.5, length=None, vp=3000.0, vs=1700.0, rho=2300.0, amplitude=0.10,
+                 sigma=150.0):
+    """3-D triclinic medium: isotropic background (vp, vs, rho) plus a smooth random perturbation of
+    all 21 stiffness constants.
+
+    Each of the 21 perturbation fields is seeded white noise filtered by a Gaussian of ``sigma`` m;
+    the symmetric 6x6 perturbation is scaled so that its largest spectral norm over the grid is
+    ``amplitude`` times the background's, and every node's matrix is made positive definite by
+    flooring its eigenvalues at 1/10 of the background's smallest (with 10 % amplitude the floor is
+    never reached).  ``length`` keeps the physical extent for reduced grids.  Source at the centre.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = n * h if length is None else float(length)
+    h = L / n
+    mu = rho * vs ** 2
+    lam = rho * vp ** 2 - 2 * mu
+    C0 = isotropic_voigt(lam, mu)
+    iu = np.triu_indices(6)
+    dC = np.zeros((n, n, n, 6, 6))
+    for m in range(21):
+        f = _gaussian_filter(rng.standard_normal((n, n, n)), sigma / h)
+        dC[..., iu[0][m], iu[1][m]] = f
+        dC[..., iu[1][m], iu[0][m]] = f
+    norm0 = np.linalg.norm(C0, 2)
+    dnorm = np.max(np.linalg.norm(dC.reshape(-1, 6, 6), ord=2, axis=(1, 2)))
+    C = C0 + dC * (amplitude * norm0 / dnorm)
+    w, Q = np.linalg.eigh(C)
+    floor = 0.1 * np.min(np.linalg.eigvalsh(C0))
+    C = np.einsum('...ij,...j,...kj->...ik', Q, np.maximum(w, floor), Q)
+    c21, r = _pack(C, np.full((n, n, n), rho))
+    xs = ((n // 2) * h,) * 3
+    steps = default_steps_3d(n, h, vp) if steps is None else steps
+    return Problem3D('triclinic_3d', n, n, n, h, h, h, c21, r, xs, n_theta, n_phi, list(freqs),
+                     beam_width, steps, cfl, meta=dict(seed=seed, length=L, vp=vp, vs=vs, rho=rho,
+                                                       amplitude=amplitude, sigma=sigma))

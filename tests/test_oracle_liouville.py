@@ -138,3 +138,13 @@ def test_homogeneous_vti_steady_state_closed_form(vti_small):
     assert np.max(np.abs(lab['tau'][sel] - tau_ref[sel])) < 1e-9
     # the source indicator is 1 up to the smeared edge of the tube (|b| ~ R_Sigma)
     assert np.mean(lab['q'][sel] > 0.99) > 0.99
+
+
+def test_pooled_velocity_planes_equal_the_serial_ones():
+    p = synthmedia.tti_heterogeneous(n=24, n_theta=12, length=2560.0, steps=5, freqs=(10.0,))
+    from oracle import medium as OM
+    a, dx, dz, _ = OM.medium_2d(p)
+    serial = CH.velocity_field_2d(a, dx, dz, p.n_theta)
+    pooled = L.velocity_field_pooled(p, processes=3)
+    for key in serial:
+        assert np.array_equal(serial[key], pooled[key]), key
