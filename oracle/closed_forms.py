@@ -7,7 +7,10 @@ None of these routines shares arithmetic with the Eulerian oracle they check:
 * the 2-D Helmholtz Green's function (i/4) H0^(1)(k r) (scipy's Hankel function);
 * the steady-state labels of a homogeneous medium (straight rays from the source);
 * the geometrical-optics Green's function of a homogeneous anisotropic medium, from the stationary
-  phase evaluation of its plane-wave (Fourier) representation.
+  phase evaluation of its plane-wave (Fourier) representation;
+* 3-D: the steady-state labels of a homogeneous medium, the Gaussian curvature of the VTI slowness
+  surface (from Thomsen's exact phase velocity) and the GO Green's function built on it, and the
+  continuous Gaussian-beam integral of analytic beams in a homogeneous isotropic medium.
 """
 from __future__ import annotations
 
@@ -114,3 +117,116 @@ def homogeneous_labels(theta, X, Z, ghat, p, R_sigma):
     tau = p[:, 0][:, None, None] * X[None] + p[:, 1][:, None, None] * Z[None]
     Th = np.broadcast_to(theta[:, None, None], tau.shape).copy()
     return dict(b=b, q=q, Th=Th, tau=tau)
+
+
+# ------------------------------------------------------------------------------------------------
+# 3-D
+
+def homogeneous_labels_3d(S):
+    """Steady-state labels of a homogeneous medium on every cell of a Setup3D: straight rays along
+    the source group direction g(n) of each direction cell, b = d - (d . g) g, n0 = n, tau = p . d,
+    q = 1 on the frozen manifold and on rays that passed their closest approach within R_Sigma
+    (|b| <= R_Sigma and d . g >= 0)."""
+    from .christoffel import source_quantities_3d
+    o = S.p.origin
+    X = (np.arange(S.nx) * S.hx + o[0] - S.xs[0])[None, None, None, None, :]
+    Y = (np.arange(S.ny) * S.hy + o[1] - S.xs[1])[None, None, None, :, None]
+    Z = (np.arange(S.nz) * S.hz + o[2] - S.xs[2])[None, None, :, None, None]
+    g = [S.gs[..., c][:, :, None, None, None] for c in range(3)]
+    n = [S.n[..., c][:, :, None, None, None] for c in range(3)]
+    v = source_quantities_3d(S.a_s, S.n)[0][:, :, None, None, None]
+    L = X * g[0] + Y * g[1] + Z * g[2]
+    b = [X - L * g[0], Y - L * g[1], Z - L * g[2]]
+    bn = np.sqrt(b[0] ** 2 + b[1] ** 2 + b[2] ** 2)
+    shape = np.broadcast(X, Y, Z, g[0]).shape
+    q = (S.frozen | ((bn <= S.R_sigma) & (L >= 0))).astype(np.float64)
+    out = {'bx': np.broadcast_to(b[0], shape).copy(), 'by': np.broadcast_to(b[1], shape).copy(),
+           'bz': np.broadcast_to(b[2], shape).copy(), 'q': q,
+           'tau': np.broadcast_to((n[0] * X + n[1] * Y + n[2] * Z) / v, shape).copy()}
+    for c, f in enumerate(('n0x', 'n0y', 'n0z')):
+        out[f] = np.broadcast_to(n[c], shape).copy()
+    return out
+
+
+def vti_slowness_gaussian_curvature(theta, vp0, vs0, eps, delta):
+    """Gaussian curvature of the qP slowness surface of a VTI medium at polar phase angle theta.
+
+    The surface is one of revolution about z with the meridian r(theta) = 1/v(theta) (polar form,
+    Thomsen's exact v); its curvatures are the meridian's, |r^2 + 2 r'^2 - r r''| / (r^2 + r'^2)^1.5,
+    and the parallel's, g_h / p_h (horizontal component of the unit normal, i.e. of the group
+    direction, over the distance from the axis; equal to the meridian's on the axis)."""
+    theta = np.asarray(theta, np.float64)
+    hstep = 1e-30
+    r_of = lambda t: 1.0 / thomsen_vti_phase_velocity(t, vp0, vs0, eps, delta)
+    r = r_of(theta)
+    d1 = lambda t: np.imag(r_of(t + 1j * hstep)) / hstep
+    r1 = d1(theta)
+    e = 1e-5
+    r2 = (d1(theta + e) - d1(theta - e)) / (2 * e)
+    km = np.abs(r ** 2 + 2 * r1 ** 2 - r * r2) / (r ** 2 + r1 ** 2) ** 1.5
+    v, Vx, Vz = vti_group_velocity(theta, vp0, vs0, eps, delta)
+    gh = np.abs(Vx) / np.hypot(Vx, Vz)
+    ph = np.abs(np.sin(theta)) / v
+    with np.errstate(divide='ignore', invalid='ignore'):
+        kp = np.where(ph > 1e-12, gh / ph, km)
+    return km * kp
+
+
+def homogeneous_go_green_3d_vti(X, Y, Z, omega, vp0, vs0, eps, delta):
+    """Geometrical-optics Green's function of a homogeneous VTI medium, acoustic scaling, source at
+    the origin: the stationary-phase evaluation of the plane-wave integral,
+        u = c_ref^2 exp(i omega T) / (4 pi sqrt(K) |V| r),  T = r / |V|,
+    with p* the slowness whose group velocity V points at the receiver and K the Gaussian curvature
+    of the slowness surface there (c_ref = vp0).  Returns u, T and |u|."""
+    rho_h = np.hypot(X, Y)
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    psi = np.arctan2(rho_h, Z)
+    phase_to_group = lambda th: np.arctan2(*vti_group_velocity(th, vp0, vs0, eps, delta)[1:])
+    th = group_angle_inverse(psi.ravel(), phase_to_group).reshape(np.shape(psi))
+    _, Vx, Vz = vti_group_velocity(th, vp0, vs0, eps, delta)
+    Vn = np.hypot(Vx, Vz)
+    K = vti_slowness_gaussian_curvature(th, vp0, vs0, eps, delta)
+    T = r / Vn
+    amp = vp0 ** 2 / (4 * math.pi * np.sqrt(K) * Vn * r)
+    return amp * np.exp(1j * omega * T), T, amp
+
+
+def isotropic_beam_integral_3d(X, Y, Z, omega, w0, v, r_min, n_theta=240, n_phi=480, box=None):
+    """The continuous Gaussian-beam integral of the 3-D superposition in a homogeneous isotropic
+    medium (source at the origin), by direct quadrature over take-off directions n (midpoint rule,
+    n_theta x n_phi cells), for receivers (X, Y, Z) (1-D arrays).
+
+    Each grid-plane family a (normal e_a) contributes, for every ray that crosses the receiver's
+    plane outward at s = (x . e_a)/(n . e_a) > r_min, the analytic paraxial beam of that ray
+        W (n . e_a)^2 exp(i omega (s/v + n . delta / v + m(s) (|delta|^2 - (n . delta)^2) / 2)) / (1 + v s M0)
+    with delta = x - s n, M0 = 2 i/(omega w0^2), m(s) = M0 / (1 + v s M0) (the wavefront Hessian of
+    a beam of 1/e half-width w0 at the source), W = i omega / (8 pi^2 v).  As omega grows with
+    omega w0^2 fixed relative to the distance this tends to exp(i k r)/(4 pi r).  box = (lo, hi)
+    (3-vectors) keeps only beams whose centre s n lies inside the box (a finite grid)."""
+    th = (np.arange(n_theta) + 0.5) * np.pi / n_theta
+    ph = (np.arange(n_phi) + 0.5) * 2 * np.pi / n_phi
+    TH, PH = np.meshgrid(th, ph, indexing='ij')
+    n = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    dW = (np.sin(TH) * (np.pi / n_theta) * (2 * np.pi / n_phi)).reshape(-1)
+    M0 = 2j / (omega * w0 ** 2)
+    W = 1j * omega / (8 * np.pi ** 2 * v)
+    xr = np.stack([np.ravel(X), np.ravel(Y), np.ravel(Z)], -1)
+    out = np.zeros(len(xr), np.complex128)
+    for i, x in enumerate(xr):
+        acc = 0.0
+        for a in range(3):
+            na = n[:, a]
+            with np.errstate(divide='ignore', invalid='ignore'):
+                s = x[a] / na
+            ok = np.isfinite(s) & (s > r_min)
+            if box is not None:
+                xc = np.where(ok[:, None], s[:, None] * n, 0.0)
+                ok &= np.all((xc >= np.asarray(box[0]) - 1e-9) & (xc <= np.asarray(box[1]) + 1e-9), axis=-1)
+            nn, sa, dw = n[ok], s[ok], dW[ok]
+            d = x[None, :] - sa[:, None] * nn
+            nd = np.einsum('ij,ij->i', nn, d)
+            m = M0 / (1 + v * sa * M0)
+            ph_ = omega * (sa / v + nd / v + 0.5 * m * (np.einsum('ij,ij->i', d, d) - nd ** 2))
+            acc = acc + np.sum(dw * nn[:, a] ** 2 * W * np.exp(1j * ph_) / (1 + v * sa * M0))
+        out[i] = acc
+    return out.reshape(np.shape(X))
