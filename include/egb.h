@@ -1,6 +1,6 @@
 /* egb.h — C ABI of the GB300 anisotropic Eulerian Gaussian beam library (libegb.so).
  *
- * The library computes frequency-domain qP Green's functions of a point source in a 2-D
+ * The library computes frequency-domain qP Green's functions of a point source in a 2-D or 3-D
  * anisotropic, heterogeneous elastic medium with the Eulerian Gaussian beam method of X. Huang,
  * "Eulerian Gaussian beams for high frequency wave propagation in inhomogeneous media of arbitrary
  * anisotropy" (arXiv 2006.11945).  The calls follow the paper's statement of the problem:
@@ -24,8 +24,12 @@
  *   - Ownership: the library owns media and solves (device resident until egb_release or
  *     egb_destroy).  The caller owns every buffer it passes.
  *   - Units: SI.  omega in rad/s, lengths in m, stiffness in Pa, density in kg/m^3.
- *   - Grids: 2-D node grids, x horizontal, z down, nodes at origin + i*h, stored z-major with x
- *     fastest (node = iz*nx + ix).  Phase angles theta_k = 2 pi k / n_theta, from +z toward +x.
+ *   - Grids: nodes at origin + i*h, x horizontal, z down, stored z-major with x fastest
+ *     (2-D: node = iz*nx + ix; 3-D: node = (iz*ny + iy)*nx + ix).  2-D phase angles
+ *     theta_k = 2 pi k / n_theta from +z toward +x.  3-D phase directions
+ *     n = (sin th cos ph, sin th sin ph, cos th) with polar angles at cell centres
+ *     th_j = (j + 1/2) pi / n_theta and azimuths ph_k = 2 pi k / n_phi; direction cell
+ *     dir = k * n_theta + j.
  *   - Threading: calls on one context are serialised by an internal mutex.
  */
 #ifndef EGB_H
@@ -71,12 +75,12 @@ egb_status egb_create(egb_ctx **out, int device, void *cuda_stream, const egb_op
 egb_status egb_destroy(egb_ctx *ctx);
 
 /* Upload a medium (Sec. 2: a_ijkl = c_ijkl / rho, Eq. 5).
- *   dim      2 (3-D media are rejected with EGB_E_INVALID)
- *   n        {nx, ny, nz}; ny ignored for dim 2; nx, nz >= 5
+ *   dim      2 or 3
+ *   n        {nx, ny, nz}; ny ignored for dim 2; every used extent >= 5
  *   h        {hx, hy, hz} node spacing (m, > 0); origin {ox, oy, oz} (m)
- *   c21      [nz*nx][21] float32 stiffness per node, Voigt upper triangle row by row
+ *   c21      [nodes][21] float32 stiffness per node, Voigt upper triangle row by row
  *            (C11 C12 C13 C14 C15 C16 C22 ... C66), Pa; host or device
- *   rho      [nz*nx] float32 density per node (> 0), host or device
+ *   rho      [nodes] float32 density per node (> 0), host or device
  *   out      receives the medium id
  * The device validates positive definiteness per node (6x6 Cholesky); failure is reported as
  * EGB_E_NOT_PD by the next synchronising call.  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_CUDA. */
@@ -89,11 +93,14 @@ egb_status egb_medium(egb_ctx *ctx, int dim, const int n[3], const double h[3],
  *   n_omega     number of angular frequencies (1..64); omega[n_omega] rad/s (> 0), host memory
  *   beam_width  w0 (m, > 0): the Gaussian beams' 1/e half-width along the wavefront at the source
  *               (the complex initial data of Eq. 24)
- *   n_ang       {n_theta, unused}: phase-angle samples (8..4096)
+ *   n_ang       2-D: {n_theta, unused}, phase-angle samples (8..4096); 3-D: {n_theta, n_phi}, polar
+ *               samples (2..512) and azimuth samples (even, 4..1024)
  *   r0          radius (m) of the frozen source ball; <= 0 selects 2*max(hx, hz).  Cells within
  *               R_Sigma = max(4 r0, min(Lx, Lz)/8) of x_s whose ray still approaches the source are
- *               frozen too (the closest-approach manifold that replaces Eq. 20's initial plane)
- * Allocates the phase-space state (about 3 x 20 + 24 bytes per cell) after checking free device
+ *               frozen too (the closest-approach manifold that replaces Eq. 20's initial plane;
+ *               3-D: R_Sigma = max(4 r0, min(Lx, Ly, Lz)/8), r0 default 2*max(hx, hy, hz))
+ * Allocates the phase-space state (2-D about 3 x 20 + 24 bytes per cell; 3-D about 3 x 36 + 37
+ * bytes per cell) after checking free device
  * memory (EGB_E_NOMEM otherwise), computes the characteristic velocities (Eqs. 3-12), the time
  * step bound and the initial level sets.  Synchronises the context stream once (to read the CFL
  * bound).  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_NOT_PD (medium failed validation), EGB_E_CUDA. */
@@ -101,25 +108,29 @@ egb_status egb_source(egb_ctx *ctx, egb_medium_id medium, const double xs[3], in
                       const double *omega, double beam_width, const int n_ang[2], double r0,
                       egb_solve_id *out);
 
-/* Advance the level sets `steps` TVD-RK3 steps (HJ-WENO3 in x, z, theta) at Courant number cfl
- * (0 < cfl <= 1); dt = cfl / max(|Vx|/hx + |Vz|/hz + |dtheta/dt|/dtheta).  Steps compose: calling
+/* Advance the level sets `steps` TVD-RK3 steps (HJ-WENO3 in x, z, theta; 3-D: x, y, z, theta, phi)
+ * at Courant number cfl (0 < cfl <= 1); dt = cfl / max(|Vx|/hx + |Vz|/hz + |dtheta/dt|/dtheta)
+ * (3-D: + |Vy|/hy + |dphi/dt|/dphi).  Steps compose: calling
  * twice with s1 and s2 equals one call with s1 + s2.  Asynchronous.  Errors: EGB_E_INVALID. */
 egb_status egb_evolve(egb_ctx *ctx, egb_solve_id solve, int steps, double cfl);
 
 /* Advance several solves of this context together: solve i by steps[i] TVD-RK3 steps at Courant
  * number cfl (same scheme as egb_evolve, results bit-identical to advancing each alone).  Each RK
  * stage is one persistent launch over the tiles of every solve still advancing; whole 3-step
- * rotations are captured into a CUDA graph and replayed.  Solves must use EGB_FP32_PHASE64 and be
- * distinct.  Asynchronous.  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_CUDA. */
+ * rotations are captured into a CUDA graph and replayed.  Solves must be 2-D, use EGB_FP32_PHASE64
+ * and be distinct.  Asynchronous.  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_CUDA. */
 egb_status egb_evolve_batch(egb_ctx *ctx, int n, const egb_solve_id *solves, const int *steps,
                             double cfl);
 
 /* Superpose the Gaussian beams (Eqs. 25-26, 33-35) and extract arrivals.
- *   u_out   complex64 [n_omega][nz][nx] (interleaved re, im), or NULL
- *   count   uint8 [nz][nx] number of arrivals kept per node, or NULL
- *   T       float64 [nz][nx][kmax] traveltimes (s), ascending; unused slots 0; or NULL
- *   A       float32 [nz][nx][kmax] geometrical amplitudes |u| sqrt(omega); unused 0; or NULL
+ *   u_out   complex64 [n_omega][nodes] (interleaved re, im), or NULL
+ *   count   uint8 [nodes] number of arrivals kept per node, or NULL
+ *   T       float64 [nodes][kmax] traveltimes (s), ascending; unused slots 0; or NULL
+ *   A       float32 [nodes][kmax] geometrical amplitudes, 2-D |u| sqrt(omega), 3-D |u|; unused 0;
+ *           or NULL
  *   kmax    capacity per node (1..32) when count/T/A are given
+ * 3-D: beams are centred where Gamma crosses the grid planes of constant x, y and z and evaluated
+ * in those planes; a homogeneous isotropic medium gives exp(i k r)/(4 pi r).
  * Output scaling: rho_s c_ref^2 times the scalar qP Green's function, c_ref the source phase
  * velocity along +z; a homogeneous isotropic medium gives (i/4) H0^(1)(k r); phase exp(+i omega T)
  * (Eq. 2).  Nodes with more than kmax arrivals keep the kmax earliest and latch
@@ -135,7 +146,8 @@ egb_status egb_superpose(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t 
  * loop whose device memory is already handed to a pool or caching allocator (a cudaMalloc outside
  * it can fail or fragment it), or a latency-critical loop that must not hit cudaMalloc/cudaFree
  * and their implicit device-wide synchronisation.
- * It computes exactly what egb_superpose computes, but its work buffers live in one statically
+ * It computes exactly what egb_superpose computes for 2-D solves (3-D solve ids are not accepted),
+ * but its work buffers live in one statically
  * sized device array of EGB_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  Restrictions:
  *   - u_out, count, T, A must be device pointers (or NULL); host pointers give EGB_E_INVALID;
@@ -168,19 +180,25 @@ typedef struct {
     double c_ref;          /* source qP phase velocity along +z (m/s) */
     uint64_t cells;        /* nx * nz * n_theta */
     uint64_t device_bytes; /* device memory held by the solve */
-    int tile_chunk;        /* theta planes per stencil work item chosen by the autotuner (0: FP64) */
+    int tile_chunk;        /* theta planes per stencil work item chosen by the autotuner (0: FP64 or 3-D) */
+    int dim;               /* 2 or 3 */
+    int ny;                /* 3-D: nodes along y (1 in 2-D) */
+    int n_phi;             /* 3-D: azimuth samples (1 in 2-D); n_theta is then the polar count */
 } egb_solve_info;
 
 egb_status egb_get_solve_info(egb_ctx *ctx, egb_solve_id solve, egb_solve_info *out);
 
-/* Copy the level sets of a solve to the caller: out = [4][n_theta][nz][nx] float64 holding
+/* Copy the level sets of a solve to the caller.  3-D: out = [8][n_phi][n_theta][nz][ny][nx] float64
+ * holding bx, by, bz (offset of the ray from x_s at closest approach, m), n0x, n0y, n0z (take-off
+ * phase direction), q, tau (s).  2-D: out = [4][n_theta][nz][nx] float64 holding
  * b (signed distance of the ray from x_s at closest approach, m), q (1 where the labels come from
  * the source manifold, 0 from the domain boundary), vartheta (angle label, rad), tau (s), host or
  * device.  Synchronous.  For tests and diagnostics (the state otherwise stays on the device). */
 egb_status egb_read_state(egb_ctx *ctx, egb_solve_id solve, double *out);
 
 /* Copy the characteristic velocities: out = [6][n_theta][nz][nx] float32 holding Vx, Vz,
- * dtheta/dt, v (phase velocity), dp_x/dt, dp_z/dt.  Synchronous. */
+ * dtheta/dt, v (phase velocity), dp_x/dt, dp_z/dt; 3-D: [9][n_phi][n_theta][nz][ny][nx] holding
+ * Vx, Vy, Vz, dtheta/dt, dphi/dt, v, dp_x/dt, dp_y/dt, dp_z/dt.  Synchronous. */
 egb_status egb_read_velocity(egb_ctx *ctx, egb_solve_id solve, float *out);
 
 #ifdef __cplusplus

@@ -126,7 +126,8 @@ def homogeneous_labels_3d(S):
     """Steady-state labels of a homogeneous medium on every cell of a Setup3D: straight rays along
     the source group direction g(n) of each direction cell, b = d - (d . g) g, n0 = n, tau = p . d,
     q = 1 on the frozen manifold and on rays that passed their closest approach within R_Sigma
-    (|b| <= R_Sigma and d . g >= 0)."""
+    (|b| <= R_Sigma and not approaching, with the frozen manifold's rule for d . g at rounding
+    level)."""
     from .christoffel import source_quantities_3d
     o = S.p.origin
     X = (np.arange(S.nx) * S.hx + o[0] - S.xs[0])[None, None, None, None, :]
@@ -139,7 +140,9 @@ def homogeneous_labels_3d(S):
     b = [X - L * g[0], Y - L * g[1], Z - L * g[2]]
     bn = np.sqrt(b[0] ** 2 + b[1] ** 2 + b[2] ** 2)
     shape = np.broadcast(X, Y, Z, g[0]).shape
-    q = (S.frozen | ((bn <= S.R_sigma) & (L >= 0))).astype(np.float64)
+    r2 = Z * Z + Y * Y + X * X
+    approach = (L < 0) & (L * L > 1e-24 * r2)   # the frozen manifold's tie rule
+    q = (S.frozen | ((bn <= S.R_sigma) & ~approach)).astype(np.float64)
     out = {'bx': np.broadcast_to(b[0], shape).copy(), 'by': np.broadcast_to(b[1], shape).copy(),
            'bz': np.broadcast_to(b[2], shape).copy(), 'q': q,
            'tau': np.broadcast_to((n[0] * X + n[1] * Y + n[2] * Z) / v, shape).copy()}

@@ -20,7 +20,9 @@ Labels (the 3-D form of the 2-D closest-approach labels):
 Source manifold (Eq. 20 generalised as in 2-D): a cell is frozen when |d| <= r0, or |d| <= R_Sigma
 and d . g_s(n) < 0 (g_s the source medium's unit group direction), R_Sigma = max(4 r0,
 min(Lx, Ly, Lz) / 8), r0 = 2 max(h).  The decision takes r^2 = (dz dz + dy dy) + dx dx and
-d . g_s = (dx gx + dy gy) + dz gz, each product and sum rounded in that order.
+d . g_s = (dx gx + dy gy) + dz gz, each product and sum rounded in that order; a cell counts as
+approaching only when (d . g_s)^2 > 1e-24 r^2 as well (cells on the closest-approach plane, where
+symmetric grids put d . g_s at rounding level with either sign, are leaving).
 
 Grid: nodes at origin + i h with two ghost layers in x, y, z holding the straight-ray data (media
 clamped to the nearest node) with q = 0 (Dirichlet inflow).  theta is sampled at cell centres
@@ -83,7 +85,10 @@ class Setup3D:
         r2 = dz * dz + dy * dy + dx * dx
         g = [self.gs[..., c][:, :, None, None, None] for c in range(3)]
         dot = dx * g[0] + dy * g[1] + dz * g[2]
-        self.frozen = (r2 <= self.r0 * self.r0) | ((r2 <= self.R_sigma * self.R_sigma) & (dot < 0.0))
+        # approaching: d . g_s < 0 by more than 1e-12 |d| (a cell on the closest-approach plane, where
+        # d . g_s is rounding noise of either sign, belongs to the leaving half)
+        approach = (dot < 0.0) & (dot * dot > 1e-24 * r2)
+        self.frozen = (r2 <= self.r0 * self.r0) | ((r2 <= self.R_sigma * self.R_sigma) & approach)
         v = self.vel
         rate = (np.abs(v['Vx']) / self.hx + np.abs(v['Vy']) / self.hy + np.abs(v['Vz']) / self.hz
                 + np.abs(v['thetadot']) / self.dth + np.abs(v['phidot']) / self.dph)

@@ -416,3 +416,46 @@ def green3d(S, lab, omegas, beam_width):
                     else:
                         u[io, :, :, plane] += contrib[q_].T
     return u
+
+
+def ambiguous_nodes3d(S, lab, tol=1e-4, q_band=0.05, spur_band=1e-3):
+    """Nodes whose arrival count hinges on a decision below the rounding of an FP32 evaluation, for
+    triangles of the direction sphere that (nearly) contain the projected origin (barycentric
+    weights all >= -tol) and (nearly) pass the |b . r_hat| <= |x - x_s|/4 test: the origin within
+    a relative distance tol of the triangle's boundary with every vertex flagged; a vertex source
+    indicator within q_band of 1/2 (no vertex frozen); or |b . r_hat| within a relative spur_band of
+    the bound with every vertex flagged."""
+    nz, ny, nx = S.nz, S.ny, S.nx
+    X = (np.arange(nx) * S.hx + S.p.origin[0] - S.xs[0])[None, None, :]
+    Y = (np.arange(ny) * S.hy + S.p.origin[1] - S.xs[1])[None, :, None]
+    Z = (np.arange(nz) * S.hz + S.p.origin[2] - S.xs[2])[:, None, None]
+    D = np.stack(np.broadcast_arrays(X, Y, Z), -1)
+    r = np.linalg.norm(D, axis=-1)
+    rhat = D / np.where(r > 0, r, 1.0)[..., None]
+    e1, e2 = frame(np.where((r > S.r0)[..., None], rhat, np.array([0.0, 0.0, 1.0])))
+    b = np.stack([lab['bx'], lab['by'], lab['bz']], -1)
+    beta = np.stack([np.einsum('...i,...i->...', b, e1[None, None]),
+                     np.einsum('...i,...i->...', b, e2[None, None])], -1)
+    brad = np.einsum('...i,...i->...', b, rhat[None, None])
+    q = lab['q']
+    flag = _flags(S, lab)
+    out = np.zeros((nz, ny, nx), bool)
+    lim = 0.25 * r
+    for t in sphere_triangles(S.nth, S.nph):
+        P = [beta[kk, jj] for kk, jj in t]
+        area = _cross2(P[1] - P[0], P[2] - P[0])
+        with np.errstate(divide='ignore', invalid='ignore', over='ignore'):
+            w = [_cross2(P[1], P[2]) / area, _cross2(P[2], P[0]) / area, _cross2(P[0], P[1]) / area]
+            wmin = np.minimum(np.minimum(w[0], w[1]), w[2])
+            cand = np.isfinite(wmin) & (wmin >= -tol)
+            bdot = np.where(cand, sum(np.where(cand, w[v], 0.0) * brad[t[v][0], t[v][1]] for v in range(3)), np.inf)
+        fl = flag[t[0][0], t[0][1]] & flag[t[1][0], t[1][1]] & flag[t[2][0], t[2][1]]
+        nofrozen = ~(S.frozen[t[0][0], t[0][1]] | S.frozen[t[1][0], t[1][1]] | S.frozen[t[2][0], t[2][1]])
+        passes = cand & (np.abs(bdot) <= lim * (1 + spur_band))
+        qn = np.zeros_like(cand)
+        for kk, jj in t:
+            qn |= np.abs(q[kk, jj] - 0.5) < q_band
+        out |= passes & fl & (wmin <= tol)
+        out |= passes & nofrozen & qn
+        out |= cand & fl & (np.abs(np.abs(bdot) - lim) <= spur_band * lim)
+    return out & (r > S.r0)

@@ -47,7 +47,8 @@ class egb_solve_info(ctypes.Structure):
                 ('n_omega', ctypes.c_int), ('steps_done', ctypes.c_int), ('dt', ctypes.c_double),
                 ('max_rate', ctypes.c_double), ('c_ref', ctypes.c_double),
                 ('cells', ctypes.c_uint64), ('device_bytes', ctypes.c_uint64),
-                ('tile_chunk', ctypes.c_int)]
+                ('tile_chunk', ctypes.c_int), ('dim', ctypes.c_int), ('ny', ctypes.c_int),
+                ('n_phi', ctypes.c_int)]
 
 
 _lib = None
@@ -134,10 +135,10 @@ def egb_medium(h, n, hsp, origin, c21, rho, dim=2):
     return out.value
 
 
-def egb_source(h, medium, xs, omegas: Sequence[float], beam_width, n_theta, r0=0.0):
+def egb_source(h, medium, xs, omegas: Sequence[float], beam_width, n_theta, r0=0.0, n_phi=0):
     xs_ = (ctypes.c_double * 3)(*xs)
     om = (ctypes.c_double * len(omegas))(*omegas)
-    na = (ctypes.c_int * 2)(n_theta, 0)
+    na = (ctypes.c_int * 2)(n_theta, n_phi)
     out = ctypes.c_uint64()
     _check(h, load().egb_source(h, medium, xs_, len(omegas), om, beam_width, na, r0, ctypes.byref(out)))
     return out.value
@@ -243,6 +244,46 @@ class Context:
         out = np.zeros((6, nth, nz, nx), np.float32)
         egb_read_velocity(self.h, solve, out)
         return out
+
+    # ---- 3-D ----
+    def medium_3d(self, problem):
+        return egb_medium(self.h, (problem.nx, problem.ny, problem.nz), (problem.hx, problem.hy, problem.hz),
+                          tuple(problem.origin), np.ascontiguousarray(problem.c21, np.float32),
+                          np.ascontiguousarray(problem.rho, np.float32), dim=3)
+
+    def source_3d(self, medium, problem):
+        return egb_source(self.h, medium, tuple(problem.xs), problem.omegas, problem.beam_width,
+                          problem.n_theta, problem.r0 or 0.0, n_phi=problem.n_phi)
+
+    def superpose_3d(self, solve, n_omega, nz, ny, nx, kmax=8):
+        u = np.zeros((n_omega, nz, ny, nx), np.complex64)
+        cnt = np.zeros((nz, ny, nx), np.uint8)
+        T = np.zeros((nz, ny, nx, kmax), np.float64)
+        A = np.zeros((nz, ny, nx, kmax), np.float32)
+        egb_superpose(self.h, solve, u, cnt, T, A, kmax)
+        return SolveResult(u, cnt, T, A)
+
+    def read_state_3d(self, solve, nph, nth, nz, ny, nx):
+        out = np.zeros((8, nph, nth, nz, ny, nx), np.float64)
+        egb_read_state(self.h, solve, out)
+        return out
+
+    def read_velocity_3d(self, solve, nph, nth, nz, ny, nx):
+        out = np.zeros((9, nph, nth, nz, ny, nx), np.float32)
+        egb_read_velocity(self.h, solve, out)
+        return out
+
+    def solve_problem_3d(self, problem, steps=None, kmax=8):
+        """medium -> source -> evolve -> superpose for one 3-D problem; returns (result, info)."""
+        m = self.medium_3d(problem)
+        s = self.source_3d(m, problem)
+        self.evolve(s, problem.steps if steps is None else steps, problem.cfl)
+        res = self.superpose_3d(s, len(problem.freqs), problem.nz, problem.ny, problem.nx, kmax)
+        egb_sync(self.h)
+        info = egb_get_solve_info(self.h, s)
+        egb_release(self.h, s)
+        egb_release(self.h, m)
+        return res, info
 
     def solve_problem(self, problem, steps=None, kmax=8):
         """medium -> source -> evolve -> superpose for one 2-D problem; returns (result, info)."""

@@ -69,9 +69,20 @@ void free_solve(Solve *s) {
     delete s;
 }
 
+void free_solve3d(Solve3D *s) {
+    for (auto &p : s->state) cudaFree(p);
+    cudaFree(s->vel);
+    cudaFree(s->frozen);
+    cudaFree(s->gs64);
+    cudaFree(s->src);
+    cudaFree(s->scratch);
+    delete s;
+}
+
 void free_medium(Medium *m) {
     cudaFree(m->a);
     cudaFree(m->dadx);
+    cudaFree(m->dady);
     cudaFree(m->dadz);
     cudaFree(m->rho);
     cudaFree(m->c21);
@@ -106,6 +117,116 @@ egb_status ensure_desc(egb_ctx *c, int n) {
         return fail(c, EGB_E_NOMEM, "stage descriptors");
     }
     c->desc_cap = cap;
+    return EGB_OK;
+}
+
+// A point source in a 3-D medium (the 3-D path of egb_source).
+egb_status source3d(egb_ctx *c, uint64_t mid, Medium *m, const double xs[3], int n_omega, const double *omega,
+                    double beam_width, const int n_ang[2], double r0, egb_solve_id *out) {
+    int nth = n_ang[0], nph = n_ang[1];
+    if (nth < 2 || nth > 512 || nph < 4 || nph > 1024 || nph % 2)
+        return fail(c, EGB_E_INVALID, "3-D angles: n_theta in 2..512, n_phi even in 4..1024");
+    double lo[3] = {m->ox, m->oy, m->oz};
+    double hi[3] = {m->ox + (m->nx - 1) * m->hx, m->oy + (m->ny - 1) * m->hy, m->oz + (m->nz - 1) * m->hz};
+    for (int d = 0; d < 3; ++d)
+        if (!(xs[d] >= lo[d] && xs[d] <= hi[d])) return fail(c, EGB_E_INVALID, "source outside the grid");
+    DeviceGuard dg(c->device);
+    egb_status pre = latched(c);
+    if (pre != EGB_OK) return pre;
+    Solve3D *s = new Solve3D();
+    s->medium_id = mid;
+    s->m = m;
+    Grid3D &g = s->g;
+    g.nx = m->nx; g.ny = m->ny; g.nz = m->nz; g.nth = nth; g.nph = nph;
+    g.pitch = ((m->nx + 5) + 1) / 2 * 2;
+    g.rows = m->ny + 4;
+    g.block = (int64_t)(m->nz + 4) * g.rows * g.pitch;
+    g.field = g.block * nth * nph;
+    g.nodes = (int64_t)m->nx * m->ny * m->nz;
+    g.hx = m->hx; g.hy = m->hy; g.hz = m->hz;
+    g.ox = m->ox; g.oy = m->oy; g.oz = m->oz;
+    g.dth = M_PI / nth;
+    g.dph = 2.0 * M_PI / nph;
+    for (int d = 0; d < 3; ++d) s->xs[d] = xs[d];
+    double hmax = fmax(m->hx, fmax(m->hy, m->hz));
+    s->r0 = r0 > 0 ? r0 : 2.0 * hmax;
+    s->w0 = beam_width;
+    s->omega.assign(omega, omega + n_omega);
+    double Lmin = fmin((g.nx - 1) * g.hx, fmin((g.ny - 1) * g.hy, (g.nz - 1) * g.hz));
+    s->R_sigma = fmax(4.0 * s->r0, Lmin / 8.0);
+    size_t cells = (size_t)g.nodes * nth * nph;
+    size_t state_b = (size_t)NF3 * g.field * 4;
+    s->bytes = 3 * state_b + cells * 9 * 4 + cells + (size_t)nth * nph * 24 + 32 * 4;
+    if (s->bytes + (256u << 20) > free_bytes()) {
+        delete s;
+        return fail(c, EGB_E_NOMEM, "solve needs %zu bytes of device memory", (size_t)(s->bytes));
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &p : s->state)
+        if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
+    if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 9 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->frozen, cells);
+    if (e == cudaSuccess) e = cudaMalloc(&s->gs64, sizeof(double) * 3 * nth * nph);
+    if (e == cudaSuccess) e = cudaMalloc(&s->src, 32 * 4);
+    if (e != cudaSuccess) { cudaGetLastError(); free_solve3d(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
+    float *d_rate = nullptr;
+    e = cudaMalloc(&d_rate, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_rate, 0, 4, c->stream);
+    if (e == cudaSuccess) e = solve3d_setup(*s, d_rate, c->stream);
+    float rate = 0, cref = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rate, d_rate, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cref, s->src + 22, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_rate);
+    if (e != cudaSuccess) { free_solve3d(s); return cuda_fail(c, e, "3-D solve setup"); }
+    if (!(rate > 0) || !std::isfinite(rate)) { free_solve3d(s); return fail(c, EGB_E_NUMERIC, "invalid characteristic speeds"); }
+    s->max_rate = rate;
+    s->c_ref = cref;
+    s->dt = 0.5 / rate;
+    uint64_t id = c->next_id++;
+    c->solves3d[id] = s;
+    m->solves++;
+    *out = id;
+    return EGB_OK;
+}
+
+egb_status superpose3d(egb_ctx *c, Solve3D *s, void *u_out, uint8_t *count, double *T, float *A, int kmax) {
+    bool want_arr = count || T || A;
+    if (want_arr && (kmax < 1 || kmax > 32)) return fail(c, EGB_E_INVALID, "kmax must be in 1..32");
+    DeviceGuard dg(c->device);
+    size_t need = superpose3d_scratch_bytes(*s);
+    cudaError_t e = cudaSuccess;
+    if (s->scratch_bytes < need) {
+        cudaFree(s->scratch);
+        s->scratch = nullptr;
+        s->scratch_bytes = 0;
+        e = cudaMalloc(&s->scratch, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, EGB_E_NOMEM, "superposition scratch (%zu bytes)", need); }
+        s->scratch_bytes = need;
+    }
+    size_t nodes = (size_t)s->g.nodes;
+    size_t ub = s->omega.size() * nodes * 8;
+    void *du = u_out;
+    uint8_t *dc = count;
+    double *dT = T;
+    float *dA = A;
+    bool hu = u_out && !is_device_ptr(u_out), hc = count && !is_device_ptr(count);
+    bool hT = T && !is_device_ptr(T), hA = A && !is_device_ptr(A);
+    if (hu) e = cudaMalloc(&du, ub);
+    if (e == cudaSuccess && hc) e = cudaMalloc(&dc, nodes);
+    if (e == cudaSuccess && hT) e = cudaMalloc(&dT, nodes * kmax * 8);
+    if (e == cudaSuccess && hA) e = cudaMalloc(&dA, nodes * kmax * 4);
+    if (e == cudaSuccess) e = launch_superpose3d(*s, (float2 *)du, dc, dT, dA, kmax, c->d_err, c->stream);
+    if (e == cudaSuccess && hu) e = cudaMemcpyAsync(u_out, du, ub, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hc) e = cudaMemcpyAsync(count, dc, nodes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hT) e = cudaMemcpyAsync(T, dT, nodes * kmax * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hA) e = cudaMemcpyAsync(A, dA, nodes * kmax * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && (hu || hc || hT || hA)) e = cudaStreamSynchronize(c->stream);
+    if (hu) cudaFree(du);
+    if (hc) cudaFree(dc);
+    if (hT) cudaFree(dT);
+    if (hA) cudaFree(dA);
+    if (e != cudaSuccess) return cuda_fail(c, e, "superpose (3-D)");
     return EGB_OK;
 }
 
@@ -149,8 +270,10 @@ egb_status egb_destroy(egb_ctx *c) {
         DeviceGuard dg(c->device);
         cudaStreamSynchronize(c->stream);
         for (auto &kv : c->solves) free_solve(kv.second);
+        for (auto &kv : c->solves3d) free_solve3d(kv.second);
         for (auto &kv : c->media) free_medium(kv.second);
         c->solves.clear();
+        c->solves3d.clear();
         c->media.clear();
         cudaFree(c->d_err);
         cudaFree(c->d_desc);
@@ -167,24 +290,31 @@ egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], co
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
     if (!n || !h || !origin || !c21 || !rho || !out) return fail(c, EGB_E_INVALID, "null argument");
-    if (dim != 2) return fail(c, EGB_E_INVALID, "only dim = 2 media are supported");
-    if (n[0] < 5 || n[2] < 5) return fail(c, EGB_E_INVALID, "nx and nz must be >= 5");
-    if (!(h[0] > 0) || !(h[2] > 0)) return fail(c, EGB_E_INVALID, "spacings must be > 0");
+    if (dim != 2 && dim != 3) return fail(c, EGB_E_INVALID, "dim must be 2 or 3");
+    if (n[0] < 5 || n[2] < 5 || (dim == 3 && n[1] < 5)) return fail(c, EGB_E_INVALID, "every grid extent must be >= 5");
+    if (!(h[0] > 0) || !(h[2] > 0) || (dim == 3 && !(h[1] > 0))) return fail(c, EGB_E_INVALID, "spacings must be > 0");
     DeviceGuard dg(c->device);
     Medium *m = new Medium();
+    m->dim = dim;
     m->nx = n[0];
     m->nz = n[2];
     m->hx = h[0];
     m->hz = h[2];
     m->ox = origin[0];
     m->oz = origin[2];
-    size_t nodes = (size_t)m->nx * m->nz;
-    m->bytes = nodes * 4 * (21 * 3 + 1);
+    if (dim == 3) {
+        m->ny = n[1];
+        m->hy = h[1];
+        m->oy = origin[1];
+    }
+    size_t nodes = (size_t)m->nx * m->ny * m->nz;
+    m->bytes = nodes * 4 * (21 * (dim + 1) + 1);
     if (m->bytes + (64u << 20) > free_bytes()) { delete m; return fail(c, EGB_E_NOMEM, "medium needs %zu bytes", m->bytes); }
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&m->a, nodes * 21 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->dadx, nodes * 21 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->dadz, nodes * 21 * 4);
+    if (e == cudaSuccess && dim == 3) e = cudaMalloc(&m->dady, nodes * 21 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->rho, nodes * 4);
     if (e == cudaSuccess) e = cudaMalloc(&m->c21, nodes * 21 * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_medium(m); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the medium"); }
@@ -200,7 +330,9 @@ egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], co
         if (e == cudaSuccess) e = cudaMemcpyAsync(tr, rho, nodes * 4, cudaMemcpyHostToDevice, c->stream);
         dr = tr;
     }
-    if (e == cudaSuccess) e = launch_medium_prep(*m, dc, dr, c->d_err, c->stream);
+    if (e == cudaSuccess)
+        e = dim == 3 ? launch_medium_prep3d(*m, dc, dr, c->d_err, c->stream)
+                     : launch_medium_prep(*m, dc, dr, c->d_err, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->c21, dc, nodes * 21 * 4, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess && (tc || tr)) e = cudaStreamSynchronize(c->stream);
     cudaFree(tc);
@@ -224,6 +356,7 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     for (int i = 0; i < n_omega; ++i)
         if (!(omega[i] > 0)) return fail(c, EGB_E_INVALID, "omega must be > 0");
     if (!(beam_width > 0)) return fail(c, EGB_E_INVALID, "beam width must be > 0");
+    if (it->second->dim == 3) return source3d(c, mid, it->second, xs, n_omega, omega, beam_width, n_ang, r0, out);
     int nth = n_ang[0];
     if (nth < 8 || nth > 4096) return fail(c, EGB_E_INVALID, "n_theta must be in 8..4096");
     Medium *m = it->second;
@@ -338,9 +471,19 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
 egb_status egb_evolve(egb_ctx *c, egb_solve_id sid, int steps, double cfl) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
+    if (steps < 0 || !(cfl > 0) || cfl > 1) return fail(c, EGB_E_INVALID, "steps >= 0 and 0 < cfl <= 1 required");
+    auto i3 = c->solves3d.find(sid);
+    if (i3 != c->solves3d.end()) {
+        Solve3D *s3 = i3->second;
+        DeviceGuard dg(c->device);
+        s3->dt = cfl / s3->max_rate;
+        cudaError_t e = solve3d_evolve(*s3, steps, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "3-D evolve launch");
+        s3->steps += steps;
+        return EGB_OK;
+    }
     auto it = c->solves.find(sid);
     if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
-    if (steps < 0 || !(cfl > 0) || cfl > 1) return fail(c, EGB_E_INVALID, "steps >= 0 and 0 < cfl <= 1 required");
     Solve *s = it->second;
     DeviceGuard dg(c->device);
     s->dt = cfl / s->max_rate;
@@ -368,6 +511,7 @@ egb_status egb_evolve_batch(egb_ctx *c, int n, const egb_solve_id *ids, const in
     std::vector<Solve *> sv(n);
     std::vector<int> left(n);
     for (int i = 0; i < n; ++i) {
+        if (c->solves3d.count(ids[i])) return fail(c, EGB_E_INVALID, "3-D solves are advanced with egb_evolve");
         auto it = c->solves.find(ids[i]);
         if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id in batch");
         if (it->second->fp64) return fail(c, EGB_E_INVALID, "FP64-form solves cannot be batched");
@@ -406,6 +550,8 @@ egb_status egb_superpose(egb_ctx *c, egb_solve_id sid, void *u_out, uint8_t *cou
                          float *A, int kmax) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
+    auto i3 = c->solves3d.find(sid);
+    if (i3 != c->solves3d.end()) return superpose3d(c, i3->second, u_out, count, T, A, kmax);
     auto it = c->solves.find(sid);
     if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
     bool want_arr = count || T || A;
@@ -494,6 +640,14 @@ egb_status egb_release(egb_ctx *c, uint64_t id) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard dg(c->device);
+    auto i3 = c->solves3d.find(id);
+    if (i3 != c->solves3d.end()) {
+        cudaStreamSynchronize(c->stream);
+        i3->second->m->solves--;
+        free_solve3d(i3->second);
+        c->solves3d.erase(i3);
+        return EGB_OK;
+    }
     auto is = c->solves.find(id);
     if (is != c->solves.end()) {
         cudaStreamSynchronize(c->stream);
@@ -516,9 +670,31 @@ egb_status egb_release(egb_ctx *c, uint64_t id) {
 egb_status egb_get_solve_info(egb_ctx *c, egb_solve_id sid, egb_solve_info *out) {
     if (!c || !out) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
+    auto i3 = c->solves3d.find(sid);
+    if (i3 != c->solves3d.end()) {
+        Solve3D *s3 = i3->second;
+        out->nx = s3->g.nx;
+        out->nz = s3->g.nz;
+        out->n_theta = s3->g.nth;
+        out->n_omega = (int)s3->omega.size();
+        out->steps_done = s3->steps;
+        out->dt = s3->dt;
+        out->max_rate = s3->max_rate;
+        out->c_ref = s3->c_ref;
+        out->cells = (uint64_t)s3->g.nodes * s3->g.nth * s3->g.nph;
+        out->device_bytes = s3->bytes + s3->scratch_bytes;
+        out->tile_chunk = 0;
+        out->dim = 3;
+        out->ny = s3->g.ny;
+        out->n_phi = s3->g.nph;
+        return EGB_OK;
+    }
     auto it = c->solves.find(sid);
     if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
     Solve *s = it->second;
+    out->dim = 2;
+    out->ny = 1;
+    out->n_phi = 1;
     out->nx = s->g.nx;
     out->nz = s->g.nz;
     out->n_theta = s->g.nth;
@@ -536,6 +712,21 @@ egb_status egb_get_solve_info(egb_ctx *c, egb_solve_id sid, egb_solve_info *out)
 egb_status egb_read_state(egb_ctx *c, egb_solve_id sid, double *out) {
     if (!c || !out) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
+    auto i3 = c->solves3d.find(sid);
+    if (i3 != c->solves3d.end()) {
+        Solve3D *s3 = i3->second;
+        DeviceGuard dg(c->device);
+        size_t bytes = (size_t)8 * s3->g.nodes * s3->g.nth * s3->g.nph * 8;
+        double *d = out;
+        bool host = !is_device_ptr(out);
+        cudaError_t e = cudaSuccess;
+        if (host) e = cudaMalloc(&d, bytes);
+        if (e == cudaSuccess) e = launch_read_state3d(*s3, d, c->stream);
+        if (e == cudaSuccess && host) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (host) cudaFree(d);
+        return e == cudaSuccess ? EGB_OK : cuda_fail(c, e, "read state (3-D)");
+    }
     auto it = c->solves.find(sid);
     if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
     Solve *s = it->second;
@@ -555,6 +746,15 @@ egb_status egb_read_state(egb_ctx *c, egb_solve_id sid, double *out) {
 egb_status egb_read_velocity(egb_ctx *c, egb_solve_id sid, float *out) {
     if (!c || !out) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
+    auto i3 = c->solves3d.find(sid);
+    if (i3 != c->solves3d.end()) {
+        Solve3D *s3 = i3->second;
+        DeviceGuard dg(c->device);
+        size_t bytes = (size_t)9 * s3->g.nodes * s3->g.nth * s3->g.nph * 4;
+        cudaError_t e = cudaMemcpyAsync(out, s3->vel, bytes, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        return e == cudaSuccess ? EGB_OK : cuda_fail(c, e, "read velocity (3-D)");
+    }
     auto it = c->solves.find(sid);
     if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
     Solve *s = it->second;

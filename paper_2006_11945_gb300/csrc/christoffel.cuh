@@ -140,4 +140,81 @@ __device__ __forceinline__ SrcVelT<R> source_velocity(const R *a, R s, R c) {
     return r;
 }
 
+// ---- general 3-D direction n ----------------------------------------------------------------
+// Gamma_ik = sum_jl a_ijkl n_j n_l
+template <typename R>
+__device__ __forceinline__ R gam3(const R *a, int i, int k, const R n[3]) {
+    R acc = R(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) acc += a[aidx(i, j, k, l)] * n[j] * n[l];
+    return acc;
+}
+
+template <typename R>
+__device__ __forceinline__ Sym3T<R> christoffel3d(const R *a, const R n[3]) {
+    Sym3T<R> G;
+    G.xx = gam3(a, 0, 0, n);
+    G.yy = gam3(a, 1, 1, n);
+    G.zz = gam3(a, 2, 2, n);
+    G.xy = gam3(a, 0, 1, n);
+    G.xz = gam3(a, 0, 2, n);
+    G.yz = gam3(a, 1, 2, n);
+    return G;
+}
+
+// sum_jk g_j g_k sum_l a_ijkl n_l (= v V_i on the unit direction n)
+template <typename R>
+__device__ __forceinline__ R group3(const R *a, const R g[3], const R n[3], int i) {
+    R acc = R(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R t = R(0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) t += a[aidx(i, j, k, l)] * n[l];
+            acc += g[j] * g[k] * t;
+        }
+    return acc;
+}
+
+template <typename R> struct RayVel3T { R v, V[3], pd[3]; };
+
+// Phase velocity, group velocity and dp/dt at the unit direction n: V_i = a_ijkl p_l g_j g_k,
+// dp_i/dt = -1/2 g . Gamma(d_i a, p) . g with p = n / v.
+template <typename R>
+__device__ __forceinline__ RayVel3T<R> ray_velocity3d(const R *a, const R *dax, const R *day, const R *daz,
+                                                      const R n[3]) {
+    Sym3T<R> G = christoffel3d(a, n);
+    R g[3];
+    R lam = qp_eigen(G, g);
+    RayVel3T<R> r;
+    r.v = sqrt(lam);
+    R iv = R(1) / r.v, iv2 = iv * iv;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r.V[i] = group3(a, g, n, i) * iv;
+    r.pd[0] = R(-0.5) * quad(christoffel3d(dax, n), g) * iv2;
+    r.pd[1] = R(-0.5) * quad(christoffel3d(day, n), g) * iv2;
+    r.pd[2] = R(-0.5) * quad(christoffel3d(daz, n), g) * iv2;
+    return r;
+}
+
+template <typename R> struct SrcVel3T { R v, V[3], Vn; };
+
+template <typename R>
+__device__ __forceinline__ SrcVel3T<R> source_velocity3d(const R *a, const R n[3]) {
+    Sym3T<R> G = christoffel3d(a, n);
+    R g[3];
+    R lam = qp_eigen(G, g);
+    SrcVel3T<R> r;
+    r.v = sqrt(lam);
+    R iv = R(1) / r.v;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r.V[i] = group3(a, g, n, i) * iv;
+    r.Vn = sqrt(r.V[0] * r.V[0] + r.V[1] * r.V[1] + r.V[2] * r.V[2]);
+    return r;
+}
+
 }  // namespace egb

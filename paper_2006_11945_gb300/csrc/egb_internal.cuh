@@ -87,11 +87,14 @@ struct DeviceErrors {  // bits latched by kernels, read by egb_sync
 struct Medium {
     int nx, nz;
     double hx, hz, ox, oz;
-    float *a = nullptr;     // [21][nz][nx]  a = c / rho
-    float *dadx = nullptr;  // [21][nz][nx]
-    float *dadz = nullptr;  // [21][nz][nx]
-    float *rho = nullptr;   // [nz][nx]
-    float *c21 = nullptr;   // [nz*nx][21] device copy of the input stiffness
+    int dim = 2, ny = 1;    // 3-D media: ny nodes along y at spacing hy from oy
+    double hy = 1.0, oy = 0.0;
+    float *a = nullptr;     // [21][nz][(ny)][nx]  a = c / rho
+    float *dadx = nullptr;  // [21][nz][(ny)][nx]
+    float *dady = nullptr;  // [21][nz][ny][nx] (3-D only)
+    float *dadz = nullptr;  // [21][nz][(ny)][nx]
+    float *rho = nullptr;   // [nz][(ny)][nx]
+    float *c21 = nullptr;   // [nodes][21] device copy of the input stiffness
     int solves = 0;
     size_t bytes = 0;
 };
@@ -121,6 +124,53 @@ struct Solve {
     size_t bytes = 0;
 };
 
+// ---------------------------------------------------------------------------------------------
+// 3-D phase space (x, y, z, theta, phi): n = (sin th cos ph, sin th sin ph, cos th), theta at cell
+// centres th_j = (j + 1/2) pi / n_theta, phi_k = 2 pi k / n_phi (n_phi even).  A direction cell is
+// dir = k * n_theta + j.  Every field is a stack of n_phi * n_theta blocks; a block is
+// (nz + 4) x (ny + 4) rows of `pitch` floats with the interior at z, y offsets 2 and x offset
+// XPAD3 = 2 (even, so that pairs of x-neighbours are 8-byte aligned); the two ghost layers on each
+// side hold the initial data permanently.  Fields: 0-2 b (offset of the ray from x_s at closest
+// approach), 3-5 n0 (take-off phase direction), 6 q (source indicator), 7 tau_hi, 8 tau_lo.
+// ---------------------------------------------------------------------------------------------
+constexpr int XPAD3 = 2;
+constexpr int NF3 = 9;
+
+struct Grid3D {
+    int nx, ny, nz, nth, nph;
+    int pitch;        // floats per padded row (even, >= nx + 5)
+    int rows;         // padded rows per z slice = ny + 4
+    int64_t block;    // floats per direction block = (nz + 4) * rows * pitch
+    int64_t field;    // floats per field = nph * nth * block
+    int64_t nodes;    // nx * ny * nz
+    double hx, hy, hz, ox, oy, oz, dth, dph;
+};
+
+__host__ __device__ inline int64_t pidx3(const Grid3D &g, int dir, int iz, int iy, int ix) {
+    return (int64_t)dir * g.block + ((int64_t)(iz + 2) * g.rows + (iy + 2)) * g.pitch + (ix + XPAD3);
+}
+__host__ __device__ inline int64_t cidx3(const Grid3D &g, int dir, int iz, int iy, int ix) {
+    return (int64_t)dir * g.nodes + ((int64_t)iz * g.ny + iy) * g.nx + ix;
+}
+
+struct Solve3D {
+    uint64_t medium_id;
+    Medium *m;
+    Grid3D g;
+    double xs[3], r0, w0, R_sigma;
+    std::vector<double> omega;
+    float *state[3] = {nullptr, nullptr, nullptr};  // u^n, stage buffers (NF3 padded fields each)
+    float *vel = nullptr;       // [9][cells]: Vx, Vy, Vz, thetadot, phidot, v, pdx, pdy, pdz
+    uint8_t *frozen = nullptr;  // [cells] 1 on the frozen source manifold
+    double *gs64 = nullptr;     // [dir][3] source-medium unit group direction (FP64)
+    float *src = nullptr;       // a_s[21], rho_s, c_ref
+    float *scratch = nullptr;   // superposition scratch
+    size_t scratch_bytes = 0;
+    double max_rate = 0, dt = 0, c_ref = 0;
+    int steps = 0;
+    size_t bytes = 0;
+};
+
 struct StageDesc;  // per-solve, per-stage descriptor of the batched stencil (liouville_tma.cu)
 
 struct Ctx {
@@ -132,6 +182,7 @@ struct Ctx {
     uint64_t next_id = 1;
     std::unordered_map<uint64_t, Medium *> media;
     std::unordered_map<uint64_t, Solve *> solves;
+    std::unordered_map<uint64_t, Solve3D *> solves3d;
     unsigned *d_err = nullptr;  // device error bits
     StageDesc *d_desc = nullptr;  // stage descriptors of batched launches (device)
     int desc_cap = 0;             // capacity in solves (9 descriptors per solve)
@@ -168,5 +219,17 @@ cudaError_t fp64_setup(Solve &sv, float *d_rate, cudaStream_t s);
 cudaError_t launch_rk3_step64(Solve &sv, double dt, cudaStream_t s);
 cudaError_t fp64_to_fp32_state(Solve &sv, cudaStream_t s);
 cudaError_t launch_read_state64(const Solve &sv, double *out_dev, cudaStream_t s);
+cudaError_t launch_medium_a(int nodes, const float *c21_dev, const float *rho_dev, float *a,
+                            unsigned *d_err, cudaStream_t s);
+
+// 3-D path (solve3d.cu)
+cudaError_t launch_medium_prep3d(const Medium &m, const float *c21_dev, const float *rho_dev,
+                                 unsigned *d_err, cudaStream_t s);
+cudaError_t solve3d_setup(Solve3D &sv, float *d_rate, cudaStream_t s);
+cudaError_t solve3d_evolve(Solve3D &sv, int steps, cudaStream_t s);
+size_t superpose3d_scratch_bytes(const Solve3D &sv);
+cudaError_t launch_superpose3d(Solve3D &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
+                               float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
+cudaError_t launch_read_state3d(const Solve3D &sv, double *out_dev, cudaStream_t s);
 
 }  // namespace egb

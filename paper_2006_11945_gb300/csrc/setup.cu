@@ -75,6 +75,12 @@ __global__ void k_medium_grad(int nx, int nz, double ihx, double ihz, const floa
     dadz[o] = (float)gz;
 }
 
+cudaError_t launch_medium_a(int nodes, const float *c21_dev, const float *rho_dev, float *a,
+                            unsigned *d_err, cudaStream_t s) {
+    k_medium_a<<<(nodes + 127) / 128, 128, 0, s>>>(nodes, c21_dev, rho_dev, a, d_err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const float *rho_dev,
                                unsigned *d_err, cudaStream_t s) {
     int nodes = m.nx * m.nz;
