@@ -56,6 +56,11 @@ def stencil_traffic_per_launch(cells):
     return STENCIL_TRAFFIC['bytes_per_cell_launch'] * cells
 
 
+# 3-D: the state (six FP32 labels b, n0, the indicator q and the double-float tau: 36 B) read and
+# written once per step, plus the five stored characteristic velocities (20 B) read once.
+ALGO_BYTES_PER_CELL_UPDATE_3D = 92.0
+
+
 def workload(name):
     if name == 'tti512':
         return synthmedia.tti_heterogeneous(n=512, h=5.0, n_theta=256, freqs=(10.0, 20.0, 40.0))
@@ -64,6 +69,10 @@ def workload(name):
     if name == 'tti256':
         return synthmedia.tti_heterogeneous(n=256, n_theta=256, length=2560.0, steps=1400,
                                             freqs=(10.0, 20.0, 40.0))
+    if name == 'tri96':
+        return synthmedia.triclinic_3d(n=96, h=10.0, n_theta=24, n_phi=48, freqs=(15.0,))
+    if name == 'tri48':
+        return synthmedia.triclinic_3d(n=48, n_theta=12, n_phi=24, length=960.0, freqs=(15.0,))
     if name == 'tti128':
         return synthmedia.tti_heterogeneous(n=128, n_theta=128, length=2560.0, steps=400,
                                             freqs=(10.0, 20.0, 40.0))
@@ -268,6 +277,80 @@ def run_egb(args):
         dist.destroy_process_group()
 
 
+def run_egb3d(args):
+    """The 3-D (5-D phase space) workload: whole solves (medium, source, evolve, superpose) through
+    the C ABI with --evolve-steps TVD-RK3 steps each (default 20 of the workload's full count)."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    torch.cuda.set_device(0)
+    p = workload(args.workload)
+    steps_evolve = args.evolve_steps or 20
+    stream = torch.cuda.Stream()
+    ctx = egb.Context(0, stream.cuda_stream)
+    c21_d = torch.from_numpy(np.ascontiguousarray(p.c21)).cuda()
+    rho_d = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    no, kmax = len(p.freqs), 8
+    nodes = p.nx * p.ny * p.nz
+    u_d = torch.empty((no, nodes, 2), dtype=torch.float32, device='cuda')
+    cnt_d = torch.empty((nodes,), dtype=torch.uint8, device='cuda')
+    T_d = torch.empty((nodes, kmax), dtype=torch.float64, device='cuda')
+    A_d = torch.empty((nodes, kmax), dtype=torch.float32, device='cuda')
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evolve_ms = []
+
+    def solve():
+        m = egb.egb_medium(ctx.h, (p.nx, p.ny, p.nz), (p.hx, p.hy, p.hz), tuple(p.origin), c21_d, rho_d, dim=3)
+        s = egb.egb_source(ctx.h, m, tuple(p.xs), p.omegas, p.beam_width, p.n_theta, 0.0, n_phi=p.n_phi)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+        egb.egb_evolve(ctx.h, s, steps_evolve, p.cfl)
+        with torch.cuda.stream(stream):
+            ev1.record(stream)
+        egb.egb_superpose(ctx.h, s, u_d, cnt_d, T_d, A_d, kmax)
+        egb.egb_sync(ctx.h)
+        evolve_ms.append(ev0.elapsed_time(ev1))
+        info = egb.egb_get_solve_info(ctx.h, s)
+        egb.egb_release(ctx.h, s)
+        egb.egb_release(ctx.h, m)
+        return info
+
+    for _ in range(args.warmup):
+        solve()
+    evolve_ms.clear()
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+        for _ in range(args.steps):
+            info = solve()
+        with torch.cuda.stream(stream):
+            t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    cells = info['cells']
+    launch_ms = float(np.mean(evolve_ms)) / (3 * steps_evolve)
+    achieved = ALGO_BYTES_PER_CELL_UPDATE_3D * cells / 3.0 / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    print(json.dumps({
+        'metric': 'phase-space cell-updates/s', 'value': cells * steps_evolve * args.steps / (ms / 1e3),
+        'unit': 'cell-updates/s', 'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup,
+        'ms_per_step': ms / args.steps, 'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': 'f32 (double-float tau and phase)', 'data': 'synthetic (seeded triclinic medium)',
+        'config': {'workload': f'{p.name} {p.nx}^3 at {p.hx:g} m x {p.n_theta} polar x {p.n_phi} azimuth, '
+                               f'{steps_evolve} of {p.steps} TVD-RK3 steps per solve, {len(p.freqs)} frequency',
+                   'cells': cells, 'evolve_steps': steps_evolve, 'device_GB': info['device_bytes'] / 1e9,
+                   'l2': 'state larger than L2, no flush'},
+        'evolve_cell_updates_per_s': cells * steps_evolve / (float(np.mean(evolve_ms)) / 1e3),
+        'roofline': {'bound': 'hbm', 'kernel': 'k_rk3_3d', 'achieved': achieved, 'peak': peak, 'unit': 'GB/s',
+                     'frac': achieved / peak, 'traffic': None, 'peak_kind': peak_kind, 'launch_ms': launch_ms},
+        'gpu_launches': (2 + 4 + 3 * steps_evolve + 5) * args.steps,
+        'clocks': clk.summary(),
+    }))
+    ctx.close()
+
+
 def fp64_form(p, steps, device):
     """The plain all-FP64 GPU form on the same workload, evolution timed over `steps` steps.
 
@@ -415,7 +498,8 @@ def main():
     ap.add_argument('--steps', type=int, default=3)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
-    ap.add_argument('--workload', default='tti512', choices=['tti512', 'tti256', 'tti128', 'vti64', 'serve'])
+    ap.add_argument('--workload', default='tti512',
+                    choices=['tti512', 'tti256', 'tti128', 'vti64', 'tri96', 'tri48', 'serve'])
     ap.add_argument('--serve-seconds', type=float, default=2.0)
     ap.add_argument('--serve-large-scale', type=float, default=1.0)
     ap.add_argument('--serve-chunk', type=int, default=60)
@@ -429,6 +513,8 @@ def main():
         run_reference(args)
     elif args.workload == 'serve':
         run_serve(args)
+    elif args.workload in ('tri96', 'tri48'):
+        run_egb3d(args)
     else:
         run_egb(args)
 
