@@ -19,13 +19,14 @@ Labels (the 3-D form of the 2-D closest-approach labels):
   tau                 traveltime since closest approach; p . d on the frozen manifold
 Source manifold (Eq. 20 generalised as in 2-D): a cell is frozen when |d| <= r0, or |d| <= R_Sigma
 and d . g_s(n) < 0 (g_s the source medium's unit group direction), R_Sigma = max(4 r0,
-min(Lx, Ly, Lz) / 8), r0 = 2 max(h).  The decision takes r^2 = (dz dz + dy dy) + dx dx and
+min(Lx, Ly, Lz) / 8, 2 dA r_far) (dA the angular spacing, r_far the farthest corner), r0 = 2 max(h).  The decision takes r^2 = (dz dz + dy dy) + dx dx and
 d . g_s = (dx gx + dy gy) + dz gz, each product and sum rounded in that order; a cell counts as
 approaching only when (d . g_s)^2 > 1e-24 r^2 as well (cells on the closest-approach plane, where
 symmetric grids put d . g_s at rounding level with either sign, are leaving).
 
 Grid: nodes at origin + i h with two ghost layers in x, y, z holding the straight-ray data (media
-clamped to the nearest node) with q = 0 (Dirichlet inflow).  theta is sampled at cell centres
+clamped to the nearest node), the indicator included: q = 1 where the straight ray passed its closest
+approach within R_Sigma (outflow through the source-ray tube), 0 elsewhere (Dirichlet inflow).  theta is sampled at cell centres
 th_j = (j + 1/2) pi / n_theta and continues across a pole onto the opposite azimuth (the point
 (-th, ph) is (th, ph + pi), and (pi + th, ph) is (pi - th, ph + pi)); phi is periodic.
 
@@ -48,9 +49,18 @@ GHOST = 2
 
 
 def source_disc_radius_3d(problem, r0):
-    """R_Sigma = max(4 r0, min(Lx, Ly, Lz) / 8)."""
+    """R_Sigma = max(4 r0, min(Lx, Ly, Lz) / 8, 2 dA r_far): the last term keeps the source-ray
+    tube, which subtends R_Sigma / r at distance r, wider than two angular cells at the farthest
+    node (dA = max(pi / n_theta, 2 pi / n_phi), r_far the largest distance from x_s to a corner),
+    so that every direction cell around an arrival carries source labels."""
     L = min((problem.nx - 1) * problem.hx, (problem.ny - 1) * problem.hy, (problem.nz - 1) * problem.hz)
-    return max(4.0 * r0, L / 8.0)
+    dA = max(math.pi / problem.n_theta, 2.0 * math.pi / problem.n_phi)
+    far2 = 0.0
+    for c, n, h, o in ((problem.xs[0], problem.nx, problem.hx, problem.origin[0]),
+                       (problem.xs[1], problem.ny, problem.hy, problem.origin[1]),
+                       (problem.xs[2], problem.nz, problem.hz, problem.origin[2])):
+        far2 += max((c - o) ** 2, (o + (n - 1) * h - c) ** 2)
+    return max(4.0 * r0, L / 8.0, 2.0 * dA * math.sqrt(far2))
 
 
 class Setup3D:
@@ -119,8 +129,16 @@ class Setup3D:
               'tau': (n[0] * X + n[1] * Y + n[2] * Z) / v}
         for c, f in enumerate(('n0x', 'n0y', 'n0z')):
             st[f] = np.broadcast_to(n[c], v.shape).copy()
-        q = np.zeros(v.shape)
-        q[:, :, G:-G, G:-G, G:-G][self.frozen] = 1.0
+        # indicator: the frozen manifold inside; on the ghost layers the straight-ray value, 1 on rays
+        # that passed their closest approach within R_Sigma (|b| <= R_Sigma, not approaching) and 0
+        # elsewhere, so that outflow ghosts continue the source-ray tube instead of cutting it
+        bn = np.sqrt(st['bx'] ** 2 + st['by'] ** 2 + st['bz'] ** 2)
+        r2 = Z * Z + Y * Y + X * X
+        approach = (dg < 0.0) & (dg * dg > 1e-24 * r2)
+        q = ((bn <= self.R_sigma) & ~approach).astype(np.float64)
+        inner = q[:, :, G:-G, G:-G, G:-G]
+        inner[...] = 0.0
+        inner[self.frozen] = 1.0
         st['q'] = q
         return st
 

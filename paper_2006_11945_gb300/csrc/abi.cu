@@ -152,8 +152,20 @@ egb_status source3d(egb_ctx *c, uint64_t mid, Medium *m, const double xs[3], int
     s->r0 = r0 > 0 ? r0 : 2.0 * hmax;
     s->w0 = beam_width;
     s->omega.assign(omega, omega + n_omega);
+    // R_Sigma = max(4 r0, min(L)/8, 2 dA r_far): the source-ray tube stays wider than two angular
+    // cells at the farthest corner (dA the angular spacing)
     double Lmin = fmin((g.nx - 1) * g.hx, fmin((g.ny - 1) * g.hy, (g.nz - 1) * g.hz));
-    s->R_sigma = fmax(4.0 * s->r0, Lmin / 8.0);
+    double dA = fmax(M_PI / nth, 2.0 * M_PI / nph);
+    double far2 = 0.0;
+    {
+        double c[3] = {xs[0], xs[1], xs[2]}, o[3] = {g.ox, g.oy, g.oz}, h[3] = {g.hx, g.hy, g.hz};
+        int n[3] = {g.nx, g.ny, g.nz};
+        for (int d = 0; d < 3; ++d) {
+            double a = (c[d] - o[d]) * (c[d] - o[d]), b = (o[d] + (n[d] - 1) * h[d] - c[d]);
+            far2 += fmax(a, b * b);
+        }
+    }
+    s->R_sigma = fmax(fmax(4.0 * s->r0, Lmin / 8.0), 2.0 * dA * sqrt(far2));
     size_t cells = (size_t)g.nodes * nth * nph;
     size_t state_b = (size_t)NF3 * g.field * 4;
     s->bytes = 3 * state_b + cells * 9 * 4 + cells + (size_t)nth * nph * 24 + 32 * 4;

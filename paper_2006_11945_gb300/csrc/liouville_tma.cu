@@ -22,16 +22,23 @@
 namespace egb {
 
 namespace tma {
-constexpr int TX = 64, TZ = 8;                     // tile (cells)
-constexpr int HX = TX + 8, HZ = TZ + 4;            // halo box (x -4..67, z -2..9)
-constexpr int RING = 7, RING2 = 3;                 // plane slots, centre-plane slots
-constexpr int HALO_FLOATS = NFIELD * HZ * HX;      // 4320
-constexpr int UN_FLOATS = NFIELD * TZ * TX;        // 2560
-constexpr int V_FLOATS = 3 * TZ * TX;              // 1536
-constexpr int SLOT2_FLOATS = UN_FLOATS + V_FLOATS;
-constexpr size_t SMEM_BYTES = sizeof(float) * ((size_t)RING * HALO_FLOATS + (size_t)RING2 * SLOT2_FLOATS) +
+constexpr int TX = 64, TZ = 6;                     // tile (cells)
+constexpr int HX = TX + 8, HZ = TZ + 4;            // halo box (x -4..67, z -2..TZ+1)
+constexpr int RING = 6, RING2 = 2;                 // plane slots, centre-plane slots
+constexpr int CTAS_PER_SM = 2;                     // two CTAs resident per SM (shared memory < 114 KB each)
+constexpr int HALO_FLOATS = NFIELD * HZ * HX;      // floats one halo copy brings
+constexpr int UN_FLOATS = NFIELD * TZ * TX;        // floats of the u^n copy
+constexpr int V_FLOATS = 3 * TZ * TX;              // floats of the velocity copy
+// every TMA destination starts on a 128-byte boundary: slots are padded to multiples of 32 floats
+constexpr int pad32(int n) { return (n + 31) / 32 * 32; }
+constexpr int HALO_STRIDE = pad32(HALO_FLOATS);
+constexpr int UN_STRIDE = pad32(UN_FLOATS);
+constexpr int SLOT2_STRIDE = UN_STRIDE + pad32(V_FLOATS);
+static_assert((HALO_STRIDE * 4) % 128 == 0 && (UN_STRIDE * 4) % 128 == 0 && (SLOT2_STRIDE * 4) % 128 == 0,
+              "TMA destinations must stay 128-byte aligned");
+constexpr size_t SMEM_BYTES = sizeof(float) * ((size_t)RING * HALO_STRIDE + (size_t)RING2 * SLOT2_STRIDE) +
                               8 * (RING + RING2);
-constexpr int THREADS = 256;
+constexpr int THREADS = 32 * TZ;
 }  // namespace tma
 
 // One solve, one RK stage.  Lives in device memory; a launch processes the work items of several
@@ -135,13 +142,13 @@ __device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5]
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(tma::THREADS, 1)
+__global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
     k_rk3_tma(const StageDesc *__restrict__ D, int nsolves, int total_items, unsigned *err) {
     using namespace tma;
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = reinterpret_cast<float *>(smem);
-    float *ring2 = ring + RING * HALO_FLOATS;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ring2 + RING2 * SLOT2_FLOATS);
+    float *ring2 = ring + RING * HALO_STRIDE;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ring2 + RING2 * SLOT2_STRIDE);
     uint64_t *bar2 = bar + RING;
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
     uint32_t phase = 0, phase2 = 0;      // parity bit per slot (identical in every thread)
     uint32_t pending = 0, pending2 = 0;  // slots with a copy in flight (thread 0 only)
     const uint32_t bytes_halo = HALO_FLOATS * 4;
-    const uint32_t bytes2 = (STAGE == 1 ? V_FLOATS : SLOT2_FLOATS) * 4;
+    const uint32_t bytes2 = (STAGE == 1 ? V_FLOATS : UN_FLOATS + V_FLOATS) * 4;
     int si = 0;
 
     for (int gitem = blockIdx.x; gitem < total_items; gitem += gridDim.x) {
@@ -176,16 +183,16 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
         auto issue = [&](int j) {
             int s = j % RING;
             mbar_expect_tx(bar + s, bytes_halo);
-            tma_load_4d(ring + s * HALO_FLOATS, A.mapK, x0, z0, plane_of(j), 0, bar + s);
+            tma_load_4d(ring + s * HALO_STRIDE, A.mapK, x0, z0, plane_of(j), 0, bar + s);
             pending |= 1u << s;
         };
         auto issue2 = [&](int j) {
             int s = j % RING2;
             mbar_expect_tx(bar2 + s, bytes2);
-            float *dst = ring2 + s * SLOT2_FLOATS;
+            float *dst = ring2 + s * SLOT2_STRIDE;
             int k = k0 + j;
             if (STAGE != 1) tma_load_4d(dst, A.mapN, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
-            tma_load_4d(dst + UN_FLOATS, A.mapV, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
+            tma_load_4d(dst + UN_STRIDE, A.mapV, x0 + XPAD, z0 + ZPAD, k, 0, bar2 + s);
             pending2 |= 1u << s;
         };
         if (tid == 0) {
@@ -217,14 +224,14 @@ __global__ void __launch_bounds__(tma::THREADS, 1)
             const int k = k0 + kk;
             const float *slot[5];
 #pragma unroll
-            for (int m = 0; m < 5; ++m) slot[m] = ring + ((kk + m) % RING) * HALO_FLOATS;
-            const float *s2 = ring2 + (kk % RING2) * SLOT2_FLOATS;
+            for (int m = 0; m < 5; ++m) slot[m] = ring + ((kk + m) % RING) * HALO_STRIDE;
+            const float *s2 = ring2 + (kk % RING2) * SLOT2_STRIDE;
             if (ok && row_ok && ixa < g.nx) {
                 const int ci = (tz + 2) * HX + 2 * tx + 4;   // centre (first cell) in a halo slot
                 const int cn = tz * TX + 2 * tx;             // centre in an interior slot
-                const float2 vx = *reinterpret_cast<const float2 *>(s2 + UN_FLOATS + cn);
-                const float2 vz = *reinterpret_cast<const float2 *>(s2 + UN_FLOATS + TZ * TX + cn);
-                const float2 vt = *reinterpret_cast<const float2 *>(s2 + UN_FLOATS + 2 * TZ * TX + cn);
+                const float2 vx = *reinterpret_cast<const float2 *>(s2 + UN_STRIDE + cn);
+                const float2 vz = *reinterpret_cast<const float2 *>(s2 + UN_STRIDE + TZ * TX + cn);
+                const float2 vt = *reinterpret_cast<const float2 *>(s2 + UN_STRIDE + 2 * TZ * TX + cn);
                 float2 L[4];
                 float2 ukc[NFIELD];
                 auto gather = [&](int f, float2 sx[5], float2 sz[5], float2 st[5]) {
@@ -438,7 +445,7 @@ static StageDesc make_desc(const Solve &sv, int stage, int r, int chunk) {
 }
 
 static void launch_stage(int stage, const StageDesc *d, int nsolves, int total, unsigned *err, cudaStream_t s) {
-    int sms = sm_count();
+    int sms = sm_count() * tma::CTAS_PER_SM;
     int grid = total < sms ? total : sms;
     if (grid < 1) return;
     if (stage == 1) k_rk3_tma<1><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);

@@ -297,8 +297,9 @@ __global__ void k_frozen3d(Grid3D g, const double *__restrict__ gs64, double xs,
 }
 
 // Straight-ray data of the local medium (media clamped to the nearest node for ghosts):
-// b = d - (d . g) g, n0 = n, q = 1 on the frozen manifold else 0, tau = n . d / v.
-__global__ void k_init3d(Grid3D g, double xs, double ys, double zs, const float *__restrict__ vel,
+// b = d - (d . g) g, n0 = n, tau = n . d / v; q = 1 on the frozen manifold, 0 on the other interior
+// cells, and on the ghosts 1 where the straight ray passed its closest approach within R_Sigma.
+__global__ void k_init3d(Grid3D g, double xs, double ys, double zs, double R, const float *__restrict__ vel,
                          const uint8_t *__restrict__ frozen, float *b0, float *b1, float *b2) {
     __shared__ double nd[3];
     int dir = blockIdx.z;
@@ -320,10 +321,21 @@ __global__ void k_init3d(Grid3D g, double xs, double ys, double zs, const float 
     double dg = d[0] * gg[0] + d[1] * gg[1] + d[2] * gg[2];
     double tau = (nd[0] * d[0] + nd[1] * d[1] + nd[2] * d[2]) / v;
     bool interior = ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && iz >= 0 && iz < g.nz;
-    float q = (interior && frozen[cidx3(g, dir, iz, iy, ix)]) ? 1.f : 0.f;
+    double bv[3] = {d[0] - dg * gg[0], d[1] - dg * gg[1], d[2] - dg * gg[2]};
+    float q;
+    if (interior) {
+        q = frozen[cidx3(g, dir, iz, iy, ix)] ? 1.f : 0.f;
+    } else {
+        // ghosts continue the source-ray tube: 1 where the straight ray passed its closest approach
+        // within R_Sigma (not approaching the source), 0 elsewhere
+        double bn = sqrt(bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2]);
+        double r2 = d[2] * d[2] + d[1] * d[1] + d[0] * d[0];
+        bool approach = dg < 0.0 && dg * dg > 1e-24 * r2;
+        q = (bn <= R && !approach) ? 1.f : 0.f;
+    }
     float hi = (float)tau;
     float lo = (float)(tau - (double)hi);
-    float vals[NF3] = {(float)(d[0] - dg * gg[0]), (float)(d[1] - dg * gg[1]), (float)(d[2] - dg * gg[2]),
+    float vals[NF3] = {(float)bv[0], (float)bv[1], (float)bv[2],
                        (float)nd[0], (float)nd[1], (float)nd[2], q, hi, lo};
     int64_t p = (int64_t)dir * g.block + ((int64_t)blockIdx.y) * g.pitch + c;
 #pragma unroll
@@ -344,7 +356,7 @@ cudaError_t solve3d_setup(Solve3D &sv, float *d_rate, cudaStream_t s) {
     dim3 gf((g.nx + 127) / 128, g.ny * g.nz, ndir);
     k_frozen3d<<<gf, 128, 0, s>>>(g, sv.gs64, sv.xs[0], sv.xs[1], sv.xs[2], sv.r0, sv.R_sigma, sv.frozen);
     dim3 gi((g.pitch + 127) / 128, (g.nz + 4) * g.rows, ndir);
-    k_init3d<<<gi, 128, 0, s>>>(g, sv.xs[0], sv.xs[1], sv.xs[2], sv.vel, sv.frozen, sv.state[0], sv.state[1],
+    k_init3d<<<gi, 128, 0, s>>>(g, sv.xs[0], sv.xs[1], sv.xs[2], sv.R_sigma, sv.vel, sv.frozen, sv.state[0], sv.state[1],
                                 sv.state[2]);
     return cudaGetLastError();
 }

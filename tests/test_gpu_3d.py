@@ -34,7 +34,7 @@ def _vti_offset():
     mirror symmetries put zeros of b exactly on triangle edges along symmetry planes, where rounding
     the labels to FP32 alone moves beam centres across flag boundaries (the oracle's own wavefield
     changes by 2 % when its labels are rounded to FP32); off the lattice no such ties exist."""
-    p = synthmedia.vti_homogeneous_3d(n=16, n_theta=8, n_phi=16, steps=40, freqs=[30.0])
+    p = synthmedia.vti_homogeneous_3d(n=16, n_theta=8, n_phi=16, freqs=[30.0])
     h = p.hx
     return dataclasses.replace(p, xs=(p.xs[0] + 0.37 * h, p.xs[1] + 0.21 * h, p.xs[2] + 0.13 * h))
 
