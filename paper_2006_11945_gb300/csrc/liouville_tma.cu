@@ -6,11 +6,12 @@
 // with an error-free sum; wrapped angle-label differences; frozen cells of the source manifold copy
 // u^n; ghosts are never written), organised for GB300:
 //
-//  * one CTA per SM loops over work items (x-tile of 64 cells, z-tile of 8 rows, theta chunk);
+//  * two CTAs per SM (192 threads, under 114 KB of shared memory each) loop over work items
+//    (x-tile of 64 cells, z-tile of 6 rows, theta chunk);
 //  * for each theta plane a single 4-D TMA copy brings all five state fields of the tile plus its
-//    x/z halo (a 72 x 12 box: x from -4 so the copy starts on a 16-byte boundary, z from -2) into a
-//    ring of shared-memory slots; the theta stencil reads the neighbouring planes' slots, so every
-//    plane is fetched from HBM once per tile and chunk;
+//    x/z halo (a 72 x 10 box: x from -4 so the copy starts on a 16-byte boundary, z from -2) into a
+//    ring of shared-memory slots, each starting on a 128-byte boundary; the theta stencil reads the
+//    neighbouring planes' slots, so every plane is fetched from HBM once per tile and chunk;
 //  * u^n (stages 2, 3) and the stored velocities of the centre plane come by a second TMA copy;
 //  * mbarrier transaction counts track completion; every wait is bounded and a timeout latches
 //    EGB_E_TIMEOUT, drains the copies in flight and leaves the kernel;
