@@ -351,6 +351,83 @@ def run_egb3d(args):
     ctx.close()
 
 
+def run_batch(args):
+    """The uneven batch: the first --batch-count instances of the batched recipe at full size (grids
+    256^2-1024^2 at 5 m, 128-512 angles, 1-4 frequencies, one TTI medium each), resident together.
+    One bench step = every instance advanced --evolve-steps TVD-RK3 steps by egb_evolve_batch (one
+    persistent launch per stage over the work items of all instances, 3-step rotations replayed
+    from a CUDA graph) and superposed.  The same steps taken one instance at a time with egb_evolve
+    are timed for comparison."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    torch.cuda.set_device(0)
+    ps = synthmedia.batched_instances(count=args.batch_count)
+    S = args.evolve_steps or 10
+    stream = torch.cuda.Stream()
+    ctx = egb.Context(0, stream.cuda_stream)
+    ids, outs = [], []
+    for p in ps:
+        m = ctx.medium_2d(p)
+        ids.append(ctx.source_2d(m, p))
+        outs.append((torch.empty((len(p.freqs), p.nz, p.nx, 2), dtype=torch.float32, device='cuda'),
+                     torch.empty((p.nz, p.nx), dtype=torch.uint8, device='cuda'),
+                     torch.empty((p.nz, p.nx, 8), dtype=torch.float64, device='cuda'),
+                     torch.empty((p.nz, p.nx, 8), dtype=torch.float32, device='cuda')))
+    egb.egb_sync(ctx.h)
+    cells = sum(egb.egb_get_solve_info(ctx.h, s)['cells'] for s in ids)
+
+    def step():
+        egb.egb_evolve_batch(ctx.h, ids, [S] * len(ids), ps[0].cfl)
+        for s, (u, c, T, A) in zip(ids, outs):
+            egb.egb_superpose(ctx.h, s, u, c, T, A, 8)
+
+    def timed(fn, K):
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+        for _ in range(K):
+            fn()
+        with torch.cuda.stream(stream):
+            t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    for _ in range(args.warmup):
+        step()
+    with ClockSampler(0) as clk:
+        ms = timed(step, args.steps)
+    egb.egb_sync(ctx.h)
+
+    def evolve_batch_only():
+        egb.egb_evolve_batch(ctx.h, ids, [S] * len(ids), ps[0].cfl)
+
+    def evolve_one_by_one():
+        for s in ids:
+            egb.egb_evolve(ctx.h, s, S, ps[0].cfl)
+    ms_b = timed(evolve_batch_only, 1)
+    ms_1 = timed(evolve_one_by_one, 1)
+    egb.egb_sync(ctx.h)
+    value = cells * S * args.steps / (ms / 1e3)
+    print(json.dumps({
+        'metric': 'phase-space cell-updates/s', 'value': value, 'unit': 'cell-updates/s', 'n_gpus': 1,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': ms / args.steps, 'higher_is_better': True,
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32 (double-float tau and phase)',
+        'data': 'synthetic (seeded TTI media)',
+        'config': {'workload': f'uneven batch: first {len(ps)} instances of the 64 (grids '
+                               f'{min(p.nx for p in ps)}^2-{max(p.nx for p in ps)}^2 at 5 m, '
+                               f'{min(p.n_theta for p in ps)}-{max(p.n_theta for p in ps)} angles), '
+                               f'{S} TVD-RK3 steps per instance per step, all superposed',
+                   'cells': cells, 'instances': [[p.nx, p.n_theta, len(p.freqs)] for p in ps],
+                   'l2': 'state larger than L2, no flush'},
+        'evolve_batched_cell_updates_per_s': cells * S / (ms_b / 1e3),
+        'evolve_one_by_one_cell_updates_per_s': cells * S / (ms_1 / 1e3),
+        'gpu_launches': (3 * S + 5 * len(ps)) * args.steps,
+        'clocks': clk.summary(),
+    }))
+    ctx.close()
+
+
 def fp64_form(p, steps, device):
     """The plain all-FP64 GPU form on the same workload, evolution timed over `steps` steps.
 
@@ -499,7 +576,8 @@ def main():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
     ap.add_argument('--workload', default='tti512',
-                    choices=['tti512', 'tti256', 'tti128', 'vti64', 'tri96', 'tri48', 'serve'])
+                    choices=['tti512', 'tti256', 'tti128', 'vti64', 'tri96', 'tri48', 'batch', 'serve'])
+    ap.add_argument('--batch-count', type=int, default=6)
     ap.add_argument('--serve-seconds', type=float, default=2.0)
     ap.add_argument('--serve-large-scale', type=float, default=1.0)
     ap.add_argument('--serve-chunk', type=int, default=60)
@@ -515,6 +593,8 @@ def main():
         run_serve(args)
     elif args.workload in ('tri96', 'tri48'):
         run_egb3d(args)
+    elif args.workload == 'batch':
+        run_batch(args)
     else:
         run_egb(args)
 

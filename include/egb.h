@@ -99,8 +99,11 @@ egb_status egb_medium(egb_ctx *ctx, int dim, const int n[3], const double h[3],
  *               R_Sigma = max(4 r0, min(Lx, Lz)/8) of x_s whose ray still approaches the source are
  *               frozen too (the closest-approach manifold that replaces Eq. 20's initial plane;
  *               3-D: R_Sigma = max(4 r0, min(Lx, Ly, Lz)/8), r0 default 2*max(hx, hy, hz))
- * Allocates the phase-space state (2-D about 3 x 20 + 24 bytes per cell; 3-D about 3 x 36 + 37
- * bytes per cell) after checking free device
+ * The characteristic velocities depend on the medium and the phase angles only: in 2-D (FP32
+ * precision) the first solve on a medium computes them for its angle count and later solves on the
+ * same medium with the same count reuse them (the medium owns them until it is released).
+ * Allocates the phase-space state (2-D about 3 x 20 + 12 bytes per cell, plus 24 for the first
+ * source of a medium; 3-D about 3 x 36 + 37 bytes per cell) after checking free device
  * memory (EGB_E_NOMEM otherwise), computes the characteristic velocities (Eqs. 3-12), the time
  * step bound and the initial level sets.  Synchronises the context stream once (to read the CFL
  * bound).  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_NOT_PD (medium failed validation), EGB_E_CUDA. */

@@ -59,7 +59,7 @@ void free_solve(Solve *s) {
     for (auto &p : s->state) cudaFree(p);
     for (auto &p : s->state64) cudaFree(p);
     cudaFree(s->velp64);
-    cudaFree(s->vel);
+    if (!s->vel_shared) cudaFree(s->vel);
     cudaFree(s->velp);
     cudaFree(s->frozen);
     cudaFree(s->gs64);
@@ -80,6 +80,7 @@ void free_solve3d(Solve3D *s) {
 }
 
 void free_medium(Medium *m) {
+    for (auto &kv : m->vel_cache) cudaFree(kv.second.vel);
     cudaFree(m->a);
     cudaFree(m->dadx);
     cudaFree(m->dady);
@@ -403,7 +404,9 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     s->fp64 = c->opts.precision == EGB_FP64;
     size_t velp_b = (size_t)3 * g.field * (s->fp64 ? 8 : 4);
     size_t state64_b = (size_t)4 * g.field * 8;
-    s->bytes = (s->fp64 ? state_b + 3 * state64_b : 3 * state_b) + cells * 6 * 4 + velp_b + cells +
+    auto cached = s->fp64 ? m->vel_cache.end() : m->vel_cache.find(nth);
+    bool reuse = cached != m->vel_cache.end();
+    s->bytes = (s->fp64 ? state_b + 3 * state64_b : 3 * state_b) + (reuse ? 0 : cells * 6 * 4) + velp_b + cells +
                (24 + 4 * nth) * 4;
     if (s->bytes + (256u << 20) > free_bytes()) {
         delete s;
@@ -422,7 +425,12 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
         if (e == cudaSuccess) e = cudaMalloc(&s->velp, velp_b);
         if (e == cudaSuccess) e = cudaMemsetAsync(s->velp, 0, velp_b, c->stream);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 6 * 4);
+    if (reuse) {
+        s->vel = cached->second.vel;
+        s->vel_shared = true;
+    } else if (e == cudaSuccess) {
+        e = cudaMalloc(&s->vel, cells * 6 * 4);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->frozen, cells);
     if (e == cudaSuccess) e = cudaMalloc(&s->gs64, sizeof(double) * 2 * s->g.nth);
     if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
@@ -443,6 +451,13 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     if (s->fp64) {
         if (e == cudaSuccess) e = launch_source_block(*s, c->stream);
         if (e == cudaSuccess) e = fp64_setup(*s, d_rate, c->stream);
+    } else if (reuse) {
+        // velocities of an earlier source on this medium: only the source block and the padded copy
+        if (e == cudaSuccess) e = launch_source_block(*s, c->stream);
+        if (e == cudaSuccess) e = launch_velp_from_vel(*s, c->stream);
+        if (e == cudaSuccess) e = launch_frozen_mask(*s, c->stream);
+        if (e == cudaSuccess) e = launch_init_state(*s, c->stream);
+        if (e == cudaSuccess) e = launch_zero_frozen_velocity(*s, c->stream);
     } else {
         if (e == cudaSuccess) e = launch_solve_setup(*s, c->d_err, d_rate, c->stream);
         if (e == cudaSuccess) e = launch_frozen_mask(*s, c->stream);
@@ -455,7 +470,12 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d_rate);
     if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "solve setup"); }
+    if (reuse) rate = cached->second.rate;
     if (!(rate > 0) || !std::isfinite(rate)) { free_solve(s); return fail(c, EGB_E_NUMERIC, "invalid characteristic speeds"); }
+    if (!s->fp64 && !reuse) {
+        m->vel_cache[nth] = Medium::VelEntry{s->vel, rate};  // the medium owns it from now on
+        s->vel_shared = true;
+    }
     s->max_rate = rate;
     s->c_ref = cref;
     s->cur = 0;

@@ -95,6 +95,11 @@ struct Medium {
     float *dadz = nullptr;  // [21][nz][(ny)][nx]
     float *rho = nullptr;   // [nz][(ny)][nx]
     float *c21 = nullptr;   // [nodes][21] device copy of the input stiffness
+    // characteristic velocities of the 2-D FP32 path per angle count: they depend on the medium and
+    // the phase angles only, so every source on this medium shares them (owned here, freed with
+    // the medium)
+    struct VelEntry { float *vel; float rate; };
+    std::unordered_map<int, VelEntry> vel_cache;
     int solves = 0;
     size_t bytes = 0;
 };
@@ -111,6 +116,7 @@ struct Solve {
     float *state[3] = {nullptr, nullptr, nullptr};  // three padded buffers of NFIELD fields
     int cur = 0;                                     // buffer holding u^n
     float *vel = nullptr;   // [6][nth][nz][nx]: Vx, Vz, thetadot, v, pdx, pdz
+    bool vel_shared = false;  // vel belongs to the medium's cache
     float *velp = nullptr;  // [3][nth][nz+4][pitch]: Vx, Vz, thetadot in the padded state layout
     void *tma = nullptr;    // tensor maps of the TMA stencil
     bool fp64 = false;      // plain all-FP64 form
@@ -196,6 +202,7 @@ struct Ctx {
 cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const float *rho_dev,
                                unsigned *d_err, cudaStream_t s);
 cudaError_t launch_solve_setup(const Solve &sv, unsigned *d_err, float *d_rate, cudaStream_t s);
+cudaError_t launch_velp_from_vel(const Solve &sv, cudaStream_t s);
 cudaError_t launch_init_state(const Solve &sv, cudaStream_t s);
 cudaError_t launch_frozen_mask(const Solve &sv, cudaStream_t s);
 cudaError_t launch_zero_frozen_velocity(const Solve &sv, cudaStream_t s);

@@ -185,6 +185,25 @@ __global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, fl
     }
 }
 
+// Padded velocity copy (Vx, Vz, thetadot) of the TMA stencil from the stored velocities, for a
+// solve that reuses the velocities of an earlier source on the same medium.
+__global__ void k_velp_from_vel(Grid2D g, const float *__restrict__ vel, float *__restrict__ velp) {
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y, k = blockIdx.z;
+    if (ix >= g.nx) return;
+    int64_t cells = (int64_t)g.nth * g.nx * g.nz;
+    int64_t o = cidx(g, k, iz, ix), pp = pidx(g, k, iz, ix);
+    velp[pp] = vel[o];
+    velp[g.field + pp] = vel[cells + o];
+    velp[2 * g.field + pp] = vel[2 * cells + o];
+}
+
+cudaError_t launch_velp_from_vel(const Solve &sv, cudaStream_t s) {
+    dim3 grid((sv.g.nx + 127) / 128, sv.g.nz, sv.g.nth);
+    k_velp_from_vel<<<grid, 128, 0, s>>>(sv.g, sv.vel, sv.velp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_source_block(const Solve &sv, cudaStream_t s) {
     k_source<<<(sv.g.nth + 127) / 128, 128, 0, s>>>(*sv.m, sv.xs, sv.zs, sv.g.nth, sv.src);
     return cudaGetLastError();

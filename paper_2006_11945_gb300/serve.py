@@ -32,7 +32,7 @@ class Request:
     finished: Optional[float] = None
     result: object = None
     steps_left: int = 0
-    medium: int = 0
+    medium: object = None   # backend's handle of the request's medium
     solve: int = 0
 
 
@@ -41,18 +41,61 @@ class NoMemory(Exception):
 
 
 class Backend:
-    """The egb library behind the loop (one context, one CUDA stream)."""
+    """The egb library behind the loop (one context, one CUDA stream).
 
-    def __init__(self, device=0, stream=0):
+    Requests whose problems share a stiffness array share one uploaded medium, and with it the
+    characteristic velocities the library keeps per medium and angle count; a medium stays
+    resident while a request uses it, and up to `keep_media` idle media are kept for later
+    requests (released first when the device runs short of memory)."""
+
+    def __init__(self, device=0, stream=0, keep_media=8):
         import paper_2006_11945_gb300 as egb
         self.egb = egb
         self.ctx = egb.Context(device, stream)
+        self.keep_media = keep_media
+        self.media = {}    # key -> [medium id, users, stiffness array (kept alive so its id stays unique)]
+        self.idle = []     # keys of media without users, oldest first
+
+    @staticmethod
+    def _key(p):
+        return (id(p.c21), p.nx, p.nz, p.hx, p.hz)
+
+    def _release_idle(self, keep):
+        while len(self.idle) > keep:
+            key = self.idle.pop(0)
+            mid = self.media.pop(key)[0]
+            self.egb.egb_release(self.ctx.h, mid)
+
+    def _medium(self, p):
+        key = self._key(p)
+        if key in self.media:
+            ent = self.media[key]
+            if ent[1] == 0:
+                self.idle.remove(key)
+            ent[1] += 1
+            return key, ent[0]
+        try:
+            m = self.ctx.medium_2d(p)
+        except self.egb.EgbError as e:
+            if e.status != self.egb.EGB_E_NOMEM or not self.idle:
+                raise
+            self._release_idle(0)
+            m = self.ctx.medium_2d(p)
+        self.media[key] = [m, 1, p.c21]
+        return key, m
+
+    def _unuse(self, key):
+        ent = self.media[key]
+        ent[1] -= 1
+        if ent[1] == 0:
+            self.idle.append(key)
+            self._release_idle(self.keep_media)
 
     def admit(self, req: Request):
         egb = self.egb
         p = req.problem
         try:
-            m = self.ctx.medium_2d(p)
+            key, m = self._medium(p)
         except egb.EgbError as e:
             if e.status == egb.EGB_E_NOMEM:
                 raise NoMemory() from e
@@ -60,11 +103,21 @@ class Backend:
         try:
             s = self.ctx.source_2d(m, p)
         except egb.EgbError as e:
-            egb.egb_release(self.ctx.h, m)
-            if e.status == egb.EGB_E_NOMEM:
-                raise NoMemory() from e
-            raise
-        req.medium, req.solve = m, s
+            if e.status == egb.EGB_E_NOMEM and self.idle:
+                self._release_idle(0)
+                try:
+                    s = self.ctx.source_2d(m, p)
+                except egb.EgbError as e2:
+                    self._unuse(key)
+                    if e2.status == egb.EGB_E_NOMEM:
+                        raise NoMemory() from e2
+                    raise
+            else:
+                self._unuse(key)
+                if e.status == egb.EGB_E_NOMEM:
+                    raise NoMemory() from e
+                raise
+        req.medium, req.solve = key, s
 
     def evolve(self, reqs: List[Request], steps: List[int], cfl: float):
         self.egb.egb_evolve_batch(self.ctx.h, [r.solve for r in reqs], steps, cfl)
@@ -74,7 +127,7 @@ class Backend:
         res = self.ctx.superpose(req.solve, len(p.freqs), p.nz, p.nx, req.kmax)
         self.egb.egb_sync(self.ctx.h)
         self.egb.egb_release(self.ctx.h, req.solve)
-        self.egb.egb_release(self.ctx.h, req.medium)
+        self._unuse(req.medium)
         return res
 
     def close(self):

@@ -1,5 +1,8 @@
 """Continuous batching on the GPU: requests that arrive while others run are admitted into the
-running batch, and every result equals the result of the same request solved alone."""
+running batch (requests on the same medium share it), and every result equals the result of the
+same request solved alone."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -9,9 +12,13 @@ from paper_2006_11945_gb300.serve import Request, Backend, serve
 pytestmark = pytest.mark.gpu
 
 
+_VTI = synthmedia.vti_homogeneous(n=48, n_theta=32, steps=60, freqs=(15.0, 25.0))
+
+
 def _problem(i):
     if i % 2 == 0:
-        return synthmedia.vti_homogeneous(n=48, n_theta=32, steps=60 + 7 * i, freqs=(15.0, 25.0))
+        # the even requests share one medium (and its characteristic velocities) in the backend
+        return dataclasses.replace(_VTI, steps=60 + 7 * i, xs=(_VTI.xs[0] + 10.0 * (i % 3), _VTI.xs[1]))
     return synthmedia.tti_heterogeneous(n=64, n_theta=40, length=2560.0, steps=90 + 5 * i,
                                         freqs=(10.0,), seed=20 + i)
 
