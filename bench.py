@@ -40,11 +40,11 @@ HBM_FALLBACK_GBS = 6800.0
 ALGO_BYTES_PER_CELL_UPDATE = 52.0
 # DRAM traffic of k_rk3_tma measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
 # 256 x 256 x 256 TTI case, per cell and launch, averaged over the three stage launches
-# (stage 1: 916 MB, stages 2 and 3: 1282 and 1279 MB per 16.8 M cells), with the SHA-256 of the
+# (stage 1: 917 MB, stages 2 and 3: 1285 and 1284 MB per 16.8 M cells), with the SHA-256 of the
 # kernel's device source it was taken on; traffic grows with the cells a launch processes, so the
 # figure is scaled to the timed workload.  Reported as null once the device source differs.
-STENCIL_TRAFFIC = {'bytes_per_cell_launch': (54.6 + 76.4 + 76.2) / 3.0,
-                   'device_source_sha256': '742426ef15075fd5610269a5a2b4ed5b164cc694bad6a5e69e4292d392778cd6'}
+STENCIL_TRAFFIC = {'bytes_per_cell_launch': (54.6 + 76.6 + 76.5) / 3.0,
+                   'device_source_sha256': '234b76e65aa44ff578a3fe77136950a77d740b6ec3aa9e4af51321c0f1707ba1'}
 
 
 def stencil_traffic_per_launch(cells):

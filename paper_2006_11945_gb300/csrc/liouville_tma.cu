@@ -107,39 +107,53 @@ __device__ __forceinline__ float2 wrap2(float2 d) {
     return fma2(f2(-two_pi, -two_pi), k, d);
 }
 
-// Third-order HJ-WENO for two cells (see the plain kernel for the formula).
-__device__ __forceinline__ float2 weno3_2(const float2 d[4], float2 vel, float eps) {
-    bool lx = vel.x > 0.f, ly = vel.y > 0.f;
-    float2 P = f2(lx ? d[0].x : d[3].x, ly ? d[0].y : d[3].y);
-    float2 Q = f2(lx ? d[1].x : d[2].x, ly ? d[1].y : d[2].y);
-    float2 R = f2(lx ? d[2].x : d[1].x, ly ? d[2].y : d[1].y);
-    float2 qp = sub2(Q, P), rq = sub2(R, Q);
-    float2 e2 = f2(eps, eps);
-    float2 A = fma2(qp, qp, e2);
-    float2 B = fma2(rq, rq, e2);
-    float2 B2 = mul2(B, B);
-    float2 den = fma2(mul2(A, A), f2(2.f, 2.f), B2);
-    float2 w = f2(__fdividef(B2.x, den.x), __fdividef(B2.y, den.y));
-    float2 centre = mul2(add2(d[1], d[2]), f2(0.5f, 0.5f));
-    float2 curv = add2(sub2(P, add2(Q, Q)), R);
-    return fma2(mul2(w, f2(-0.5f, -0.5f)), curv, centre);
+// Upwind side of two cells along one axis: flow towards + (the left-biased stencil) or towards -.
+struct Up2 {
+    bool lx, ly;  // cell 0 / cell 1 flows towards +
+    float2 sig;   // +1 for flow towards +, -1 otherwise
+};
+__device__ __forceinline__ Up2 upwind2(float2 v) {
+    Up2 u;
+    u.lx = v.x > 0.f;
+    u.ly = v.y > 0.f;
+    u.sig = f2(u.lx ? 1.f : -1.f, u.ly ? 1.f : -1.f);
+    return u;
 }
 
-__device__ __forceinline__ float2 deriv2(const float2 s[5], float2 vel, float eps, bool angle) {
+// Third-order HJ-WENO (the scheme of Eq. 19's spatial discretisation, as in the FP64 form) for two
+// cells, from the four consecutive differences d_0..d_3 of the five-point stencil, written with the
+// second differences e_j = d_{j+1} - d_j.  The upwind smoothness term is e_0 (flow towards +) or
+// e_2 (towards -); with A = e_up^2 + eps, B = e_1^2 + eps and w = B^2 / (B^2 + 2 A^2),
+//     2 h u_x = (d_1 + d_2) + sig w (e_up - e_1),
+// which is the central difference less w/2 times the upwind curvature (d_0 - 2 d_1 + d_2 towards +,
+// d_3 - 2 d_2 + d_1 towards -).  Returns 2 h u_x; the caller scales by velocity / (2 h).
+__device__ __forceinline__ float2 weno3_2(const float2 d[4], const Up2 &up, float2 eps2) {
+    float2 e0 = sub2(d[1], d[0]), e1 = sub2(d[2], d[1]), e2 = sub2(d[3], d[2]);
+    float2 E = f2(up.lx ? e0.x : e2.x, up.ly ? e0.y : e2.y);
+    float2 A = fma2(E, E, eps2);
+    float2 B = fma2(e1, e1, eps2);
+    float2 B2 = mul2(B, B);
+    float2 den = fma2(mul2(A, A), f2(2.f, 2.f), B2);
+    float2 num = mul2(B2, up.sig);
+    float2 w = f2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    return fma2(w, sub2(E, e1), add2(d[1], d[2]));
+}
+
+__device__ __forceinline__ float2 deriv2(const float2 s[5], const Up2 &up, float2 eps2, bool angle) {
     float2 d[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         d[j] = sub2(s[j + 1], s[j]);
         if (angle) d[j] = wrap2(d[j]);
     }
-    return weno3_2(d, vel, eps);
+    return weno3_2(d, up, eps2);
 }
 
-__device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5], float2 vel, float eps) {
+__device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5], const Up2 &up, float2 eps2) {
     float2 d[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) d[j] = add2(sub2(h[j + 1], h[j]), sub2(l[j + 1], l[j]));
-    return weno3_2(d, vel, eps);
+    return weno3_2(d, up, eps2);
 }
 
 template <int STAGE>
@@ -169,18 +183,27 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
     for (int gitem = blockIdx.x; gitem < total_items; gitem += gridDim.x) {
         while (si + 1 < nsolves && gitem >= D[si + 1].item_begin) ++si;
         const StageDesc &A = D[si];
-        const Grid2D &g = A.g;
-        const int64_t F = g.field;
+        // the descriptor's scalars live in registers for the whole item (the mbarrier waits'
+        // memory clobbers would otherwise reload them from global memory on every plane)
+        const int nx = A.g.nx, nz = A.g.nz, nth = A.g.nth, pitch = A.g.pitch;
+        const int64_t F = A.g.field, plane = A.g.plane;
+        float *const out = A.out;
+        const float2 dt2 = f2(A.dt, A.dt), cf2 = f2(A.coef, A.coef);
+        // -velocity / (2 h) per axis turns weno3_2's 2 h u_x into the -V_d du/dx_d of L(u)
+        const float hx2 = -0.5f * A.ihx, hz2 = -0.5f * A.ihz, ht2 = -0.5f * A.idth;
+        float2 eps2[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) eps2[f] = f2(A.eps[f], A.eps[f]);
         const int item = gitem - A.item_begin;
         int xt = item % A.tiles_x;
         int rest = item / A.tiles_x;
         int zt = rest % A.tiles_z;
         int ch = rest / A.tiles_z;
         int k0 = ch * A.chunk;
-        int kn = min(A.chunk, g.nth - k0);
+        int kn = min(A.chunk, nth - k0);
         int x0 = xt * TX, z0 = zt * TZ;
         int nplanes = kn + 4;
-        auto plane_of = [&](int j) { return (k0 - 2 + j + 2 * g.nth) % g.nth; };
+        auto plane_of = [&](int j) { return (k0 - 2 + j + 2 * nth) % nth; };
         auto issue = [&](int j) {
             int s = j % RING;
             mbar_expect_tx(bar + s, bytes_halo);
@@ -209,10 +232,11 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
         }
         const int iz = z0 + tz;
         const int ixa = x0 + 2 * tx;
-        const bool row_ok = iz < g.nz;
-        for (int kk = 0; kk < kn; ++kk) {
+        const bool row_ok = iz < nz;
+        int sb = 0;  // kk % RING
+        for (int kk = 0; kk < kn; ++kk, sb = (sb + 1 == RING ? 0 : sb + 1)) {
             {
-                int s = (kk + 4) % RING;
+                int s = sb + 4 >= RING ? sb + 4 - RING : sb + 4;
                 if (ok) ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u);
                 phase ^= 1u << s;
                 if (tid == 0) pending &= ~(1u << s);
@@ -225,14 +249,17 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
             const int k = k0 + kk;
             const float *slot[5];
 #pragma unroll
-            for (int m = 0; m < 5; ++m) slot[m] = ring + ((kk + m) % RING) * HALO_STRIDE;
+            for (int m = 0; m < 5; ++m) slot[m] = ring + (sb + m >= RING ? sb + m - RING : sb + m) * HALO_STRIDE;
             const float *s2 = ring2 + (kk % RING2) * SLOT2_STRIDE;
-            if (ok && row_ok && ixa < g.nx) {
+            if (ok && row_ok && ixa < nx) {
                 const int ci = (tz + 2) * HX + 2 * tx + 4;   // centre (first cell) in a halo slot
                 const int cn = tz * TX + 2 * tx;             // centre in an interior slot
                 const float2 vx = *reinterpret_cast<const float2 *>(s2 + UN_STRIDE + cn);
                 const float2 vz = *reinterpret_cast<const float2 *>(s2 + UN_STRIDE + TZ * TX + cn);
                 const float2 vt = *reinterpret_cast<const float2 *>(s2 + UN_STRIDE + 2 * TZ * TX + cn);
+                const Up2 ux_up = upwind2(vx), uz_up = upwind2(vz), ut_up = upwind2(vt);
+                const float2 cx = mul2(vx, f2(hx2, hx2)), cz = mul2(vz, f2(hz2, hz2)),
+                             ct = mul2(vt, f2(ht2, ht2));
                 float2 L[4];
                 float2 ukc[NFIELD];
                 auto gather = [&](int f, float2 sx[5], float2 sz[5], float2 st[5]) {
@@ -256,13 +283,10 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
                     // the angle label is continuous in x and z (no 2 pi seam inside a plane), so only
                     // its theta differences need wrapping
                     bool ang = (f == 2);
-                    float2 ux = deriv2(sx, vx, A.eps[f], false);
-                    float2 uz = deriv2(sz, vz, A.eps[f], false);
-                    float2 ut = deriv2(st, vt, A.eps[f], ang);
-                    float2 acc = mul2(mul2(vx, ux), f2(A.ihx, A.ihx));
-                    acc = fma2(mul2(vz, uz), f2(A.ihz, A.ihz), acc);
-                    acc = fma2(mul2(vt, ut), f2(A.idth, A.idth), acc);
-                    L[f] = f2(-acc.x, -acc.y);
+                    float2 ux = deriv2(sx, ux_up, eps2[f], false);
+                    float2 uz = deriv2(sz, uz_up, eps2[f], false);
+                    float2 ut = deriv2(st, ut_up, eps2[f], ang);
+                    L[f] = fma2(cx, ux, fma2(cz, uz, mul2(ct, ut)));
                 }
                 {
                     float2 hx5[5], hz5[5], ht5[5], lx5[5], lz5[5], lt5[5];
@@ -270,19 +294,15 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
                     gather(4, lx5, lz5, lt5);
                     ukc[3] = hx5[2];
                     ukc[4] = lx5[2];
-                    float2 ux = deriv2_ff(hx5, lx5, vx, A.eps[3]);
-                    float2 uz = deriv2_ff(hz5, lz5, vz, A.eps[3]);
-                    float2 ut = deriv2_ff(ht5, lt5, vt, A.eps[3]);
-                    float2 acc = mul2(mul2(vx, ux), f2(A.ihx, A.ihx));
-                    acc = fma2(mul2(vz, uz), f2(A.ihz, A.ihz), acc);
-                    acc = fma2(mul2(vt, ut), f2(A.idth, A.idth), acc);
-                    L[3] = sub2(f2(1.f, 1.f), acc);
+                    float2 ux = deriv2_ff(hx5, lx5, ux_up, eps2[3]);
+                    float2 uz = deriv2_ff(hz5, lz5, uz_up, eps2[3]);
+                    float2 ut = deriv2_ff(ht5, lt5, ut_up, eps2[3]);
+                    L[3] = add2(f2(1.f, 1.f), fma2(cx, ux, fma2(cz, uz, mul2(ct, ut))));
                 }
                 float2 un[NFIELD];
 #pragma unroll
                 for (int f = 0; f < NFIELD; ++f)
                     un[f] = (STAGE == 1) ? ukc[f] : *reinterpret_cast<const float2 *>(s2 + f * TZ * TX + cn);
-                const float2 dt2 = f2(A.dt, A.dt), cf2 = f2(A.coef, A.coef);
                 float2 o[NFIELD];
 #pragma unroll
                 for (int f = 0; f < 3; ++f)
@@ -297,12 +317,12 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
                 // frozen cells of the source manifold carry a zeroed velocity copy
                 const bool fa = vx.x == 0.f && vz.x == 0.f;
                 const bool fb = vx.y == 0.f && vz.y == 0.f;
-                const int64_t p = pidx(g, k, iz, ixa);
+                const int64_t p = (int64_t)k * plane + (int64_t)(iz + ZPAD) * pitch + (ixa + XPAD);
 #pragma unroll
                 for (int f = 0; f < NFIELD; ++f) {
                     float2 v = f2(fa ? un[f].x : o[f].x, fb ? un[f].y : o[f].y);
-                    if (ixa + 1 < g.nx) *reinterpret_cast<float2 *>(A.out + f * F + p) = v;
-                    else A.out[f * F + p] = v.x;
+                    if (ixa + 1 < nx) *reinterpret_cast<float2 *>(out + f * F + p) = v;
+                    else out[f * F + p] = v.x;
                 }
             }
             __syncthreads();

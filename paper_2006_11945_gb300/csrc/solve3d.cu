@@ -35,38 +35,49 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Jiang-Peng HJ-WENO3 one-sided derivative (undivided) of two cells from the differences
-// d_j = s_{j+1} - s_j of their 5-point stencils, upwinded by the sign of vel; the weight
-// 1 / (1 + 2 r^2), r = A / B, is evaluated as B^2 / (B^2 + 2 A^2).
-__device__ __forceinline__ float2 weno(const float2 d[4], float2 vel, float eps) {
-    bool lx = vel.x > 0.f, ly = vel.y > 0.f;
-    float2 P = f2(lx ? d[0].x : d[3].x, ly ? d[0].y : d[3].y);
-    float2 Q = f2(lx ? d[1].x : d[2].x, ly ? d[1].y : d[2].y);
-    float2 R = f2(lx ? d[2].x : d[1].x, ly ? d[2].y : d[1].y);
-    float2 qp = sub2(Q, P), rq = sub2(R, Q);
-    float2 e2 = f2(eps, eps);
-    float2 A = fma2(qp, qp, e2);
-    float2 B = fma2(rq, rq, e2);
-    float2 B2 = mul2(B, B);
-    float2 den = fma2(mul2(A, A), f2(2.f, 2.f), B2);
-    float2 w = f2(__fdividef(B2.x, den.x), __fdividef(B2.y, den.y));
-    float2 centre = mul2(add2(d[1], d[2]), f2(0.5f, 0.5f));
-    float2 curv = add2(sub2(P, add2(Q, Q)), R);
-    return fma2(mul2(w, f2(-0.5f, -0.5f)), curv, centre);
+// Upwind side of two cells along one axis: flow towards + (left-biased stencil) or towards -.
+struct Up2 {
+    bool lx, ly;
+    float2 sig;  // +1 towards +, -1 otherwise
+};
+__device__ __forceinline__ Up2 upwind2(float2 v) {
+    Up2 u;
+    u.lx = v.x > 0.f;
+    u.ly = v.y > 0.f;
+    u.sig = f2(u.lx ? 1.f : -1.f, u.ly ? 1.f : -1.f);
+    return u;
 }
 
-__device__ __forceinline__ float2 deriv(const float2 s[5], float2 vel, float eps) {
+// Jiang-Peng HJ-WENO3 one-sided derivative of two cells from the differences d_j = s_{j+1} - s_j
+// of their 5-point stencils, in second-difference form: with e_j = d_{j+1} - d_j, e_up = e_0
+// (flow towards +) or e_2 (towards -), A = e_up^2 + eps, B = e_1^2 + eps and the weight
+// w = 1 / (1 + 2 (A/B)^2) = B^2 / (B^2 + 2 A^2),
+//     2 h u_x = (d_1 + d_2) + sig w (e_up - e_1)
+// (the central difference less w/2 times the upwind curvature).  Returns 2 h u_x.
+__device__ __forceinline__ float2 weno(const float2 d[4], const Up2 &up, float2 eps2) {
+    float2 e0 = sub2(d[1], d[0]), e1 = sub2(d[2], d[1]), e2 = sub2(d[3], d[2]);
+    float2 E = f2(up.lx ? e0.x : e2.x, up.ly ? e0.y : e2.y);
+    float2 A = fma2(E, E, eps2);
+    float2 B = fma2(e1, e1, eps2);
+    float2 B2 = mul2(B, B);
+    float2 den = fma2(mul2(A, A), f2(2.f, 2.f), B2);
+    float2 num = mul2(B2, up.sig);
+    float2 w = f2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    return fma2(w, sub2(E, e1), add2(d[1], d[2]));
+}
+
+__device__ __forceinline__ float2 deriv(const float2 s[5], const Up2 &up, float2 eps2) {
     float2 d[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) d[j] = sub2(s[j + 1], s[j]);
-    return weno(d, vel, eps);
+    return weno(d, up, eps2);
 }
 
-__device__ __forceinline__ float2 deriv_ff(const float2 h[5], const float2 l[5], float2 vel, float eps) {
+__device__ __forceinline__ float2 deriv_ff(const float2 h[5], const float2 l[5], const Up2 &up, float2 eps2) {
     float2 d[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) d[j] = add2(sub2(h[j + 1], h[j]), sub2(l[j + 1], l[j]));
-    return weno(d, vel, eps);
+    return weno(d, up, eps2);
 }
 
 // direction cell reached from (k, j) by m steps in theta, continued across the poles
@@ -381,7 +392,7 @@ struct Stage3Args {
 constexpr int ZC3 = 8;
 
 template <int STAGE>
-__global__ void __launch_bounds__(128) k_rk3_3d(Stage3Args A) {
+__global__ void __launch_bounds__(128, 8) k_rk3_3d(Stage3Args A) {
     const Grid3D &g = A.g;
     int nxt = (g.nx + 63) / 64;
     int dir = blockIdx.x;
@@ -420,14 +431,22 @@ __global__ void __launch_bounds__(128) k_rk3_3d(Stage3Args A) {
             s[4][m] = *reinterpret_cast<const float2 *>(F + pn[m]);
         }
     };
-    auto rhs_of = [&](const float2 du[5]) {  // -(V . grad u)
-        float2 acc = mul2(mul2(vv[0], du[0]), f2(A.ih[0], A.ih[0]));
+    // upwind sides and -V_d / (2 h_d) per dimension, shared by the nine fields
+    Up2 up[5];
+    float2 cc[5];
 #pragma unroll
-        for (int d = 1; d < 5; ++d) acc = fma2(mul2(vv[d], du[d]), f2(A.ih[d], A.ih[d]), acc);
-        return f2(-acc.x, -acc.y);
+    for (int d = 0; d < 5; ++d) {
+        up[d] = upwind2(vv[d]);
+        const float c = -0.5f * A.ih[d];
+        cc[d] = mul2(vv[d], f2(c, c));
+    }
+    auto rhs_of = [&](const float2 du[5]) {  // -(V . grad u) from the 2 h u_d of weno()
+        float2 acc = mul2(cc[0], du[0]);
+#pragma unroll
+        for (int d = 1; d < 5; ++d) acc = fma2(cc[d], du[d], acc);
+        return acc;
     };
     const float2 dt2 = f2(A.dt, A.dt), cf2 = f2(A.coef, A.coef);
-    float2 res[NF3];
 #pragma unroll 1
     for (int f = 0; f < 7; ++f) {
         float2 s[5][5];
@@ -435,12 +454,15 @@ __global__ void __launch_bounds__(128) k_rk3_3d(Stage3Args A) {
         float eps = A.eps[f < 3 ? 0 : (f < 6 ? 1 : 2)];
         float2 du[5];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) du[d] = deriv(s[d], vv[d], eps);
+        for (int d = 0; d < 5; ++d) du[d] = deriv(s[d], up[d], f2(eps, eps));
         float2 L = rhs_of(du);
         float2 uc = s[0][2];
         float2 un = (STAGE == 1) ? uc : *reinterpret_cast<const float2 *>(A.un + (int64_t)f * g.field + p);
         float2 o = fma2(cf2, fma2(dt2, L, sub2(uc, un)), un);
-        res[f] = f2(fa ? un.x : o.x, fb ? un.y : o.y);
+        float2 r = f2(fa ? un.x : o.x, fb ? un.y : o.y);
+        float *O = A.out + (int64_t)f * g.field + p;
+        if (second) *reinterpret_cast<float2 *>(O) = r;
+        else *O = r.x;
     }
     {
         float2 sh[5][5], sl[5][5];
@@ -448,7 +470,7 @@ __global__ void __launch_bounds__(128) k_rk3_3d(Stage3Args A) {
         gather(8, sl);
         float2 du[5];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) du[d] = deriv_ff(sh[d], sl[d], vv[d], A.eps[3]);
+        for (int d = 0; d < 5; ++d) du[d] = deriv_ff(sh[d], sl[d], up[d], f2(A.eps[3], A.eps[3]));
         float2 L = add2(rhs_of(du), f2(1.f, 1.f));
         float2 hc = sh[0][2], lc = sl[0][2];
         float2 hn = hc, ln = lc;
@@ -459,14 +481,16 @@ __global__ void __launch_bounds__(128) k_rk3_3d(Stage3Args A) {
         float2 inc = mul2(cf2, fma2(dt2, L, add2(sub2(hc, hn), sub2(lc, ln))));
         ff ra = ff_add_f(hn.x, ln.x, inc.x);
         ff rb = ff_add_f(hn.y, ln.y, inc.y);
-        res[7] = f2(fa ? hn.x : ra.hi, fb ? hn.y : rb.hi);
-        res[8] = f2(fa ? ln.x : ra.lo, fb ? ln.y : rb.lo);
-    }
-#pragma unroll
-    for (int f = 0; f < NF3; ++f) {
-        float *O = A.out + (int64_t)f * g.field + p;
-        if (second) *reinterpret_cast<float2 *>(O) = res[f];
-        else *O = res[f].x;
+        const float2 r7 = f2(fa ? hn.x : ra.hi, fb ? hn.y : rb.hi);
+        const float2 r8 = f2(fa ? ln.x : ra.lo, fb ? ln.y : rb.lo);
+        float *O = A.out + 7 * g.field + p;
+        if (second) {
+            *reinterpret_cast<float2 *>(O) = r7;
+            *reinterpret_cast<float2 *>(O + g.field) = r8;
+        } else {
+            O[0] = r7.x;
+            O[g.field] = r8.x;
+        }
     }
     }
 }
