@@ -10,6 +10,8 @@
  *   egb_evolve    level sets advected through phase space   (Sec. 4, Eqs. 16, 19)
  *   egb_superpose Gaussian beams summed over the source manifold into u(x, omega), plus the
  *                 traveltime and amplitude of every arrival  (Sec. 5, Eqs. 25-26, 33-35)
+ *   egb_zmarch    the paper's paraxial depth march (Eqs. 13-20) with its same-row superposition,
+ *                 one call from medium to u and arrivals (one-way rays only)
  *
  * Conventions (apply to every call):
  *   - Status: every call returns egb_status; EGB_OK is 0.  No C++ exception crosses the ABI.
@@ -203,6 +205,30 @@ egb_status egb_read_state(egb_ctx *ctx, egb_solve_id solve, double *out);
  * dtheta/dt, v (phase velocity), dp_x/dt, dp_z/dt; 3-D: [9][n_phi][n_theta][nz][ny][nx] holding
  * Vx, Vy, Vz, dtheta/dt, dphi/dt, v, dp_x/dt, dp_y/dt, dp_z/dt.  Synchronous. */
 egb_status egb_read_velocity(egb_ctx *ctx, egb_solve_id solve, float *out);
+
+/* The paper's own formulation: the level sets marched in depth (Sec. 3-4, Eqs. 13-20) and the
+ * Gaussian beams centred where each depth row crosses Gamma = {X = x_s}, evaluated along that row
+ * (Sec. 5, Eqs. 25-28, 33-35).  2-D media only.  One call runs both branches from the source row:
+ * downgoing rays (phase angles theta_k = -theta_max + (k + 1/2) dtheta, dtheta = 2 theta_max /
+ * n_theta, from +z toward +x) fill the rows at and below the source, upgoing rays (the same angles
+ * + pi) the rows above it.  Every ray of a branch must keep the sign of its vertical group velocity
+ * (Eq. 13); a medium where one does not gives EGB_E_INVALID (lower theta_max).  Each row interval is
+ * crossed in ceil(h_z max(|dx/dz|/h_x + |dtheta/dz|/dtheta) / cfl) TVD-RK3 substeps.
+ *   medium     a 2-D medium id (validated: a non positive definite medium gives EGB_E_NOT_PD)
+ *   xs         source (x, y, z); z must lie on a grid row (within 1e-6 h_z), x anywhere on the grid
+ *   omega      n_omega angular frequencies (rad/s, > 0; host pointer), 0 <= n_omega <= 64
+ *   beam_width_m  w0 > 0: initial transverse beam Hessian i 2 / (omega w0^2) (Eq. 24)
+ *   n_theta    angles per branch, 4..4096; theta_max in (0, pi/2); cfl in (0, 1]
+ *   u_out      complex64 [n_omega][nz][nx] (host or device), or NULL
+ *   count, T, A   arrivals per node ([nz][nx] uint8, [nz][nx][kmax] float64 s, float32), each may
+ *              be NULL; kmax in 1..32 when any is given; more arrivals than kmax give
+ *              EGB_E_ARRIVAL_OVERFLOW after the earliest kmax are written
+ * Synchronous: returns when the outputs are written.  The work buffers (about 44 bytes per
+ * phase-space cell of the larger branch) are allocated and freed by the call; EGB_E_NOMEM when
+ * they do not fit. */
+egb_status egb_zmarch(egb_ctx *ctx, egb_medium_id medium, const double xs[3], int n_omega,
+                      const double *omega, double beam_width_m, int n_theta, double theta_max,
+                      double cfl, void *u_out, uint8_t *count, double *T, float *A, int kmax);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,7 @@ EGB_FP32_PHASE64, EGB_FP64 = 0, 1
 
 EXPORTED = ('egb_create', 'egb_destroy', 'egb_medium', 'egb_source', 'egb_evolve', 'egb_superpose',
             'egb_sync', 'egb_release', 'egb_last_error', 'egb_get_solve_info', 'egb_read_state',
-            'egb_read_velocity', 'egb_superpose_noalloc', 'egb_evolve_batch')
+            'egb_read_velocity', 'egb_superpose_noalloc', 'egb_evolve_batch', 'egb_zmarch')
 
 
 class EgbError(RuntimeError):
@@ -81,6 +81,7 @@ def load(path: Optional[str] = None):
     lib.egb_get_solve_info.argtypes = [vp, u64, P(egb_solve_info)]
     lib.egb_read_state.argtypes = [vp, u64, vp]
     lib.egb_read_velocity.argtypes = [vp, u64, vp]
+    lib.egb_zmarch.argtypes = [vp, u64, P(d), i, P(d), d, i, d, d, vp, vp, vp, vp, i]
     for name in EXPORTED:
         if name != 'egb_last_error':
             getattr(lib, name).restype = i
@@ -163,6 +164,18 @@ def egb_superpose_noalloc(h, solve, u_out=None, count=None, T=None, A=None, kmax
     """egb_superpose into caller-owned DEVICE buffers without any device allocation (the work
     buffers are a fixed 32 MiB array inside the library); see include/egb.h."""
     _check(h, load().egb_superpose_noalloc(h, solve, _ptr(u_out), _ptr(count), _ptr(T), _ptr(A), kmax))
+
+
+def egb_zmarch(h, medium, xs, omegas, beam_width, n_theta, theta_max, cfl=0.5, u_out=None, count=None,
+               T=None, A=None, kmax=8):
+    """The paper's paraxial depth march from the source row, both branches, with its same-row
+    superposition (see include/egb.h)."""
+    om = (ctypes.c_double * max(len(omegas), 1))(*[float(w) for w in omegas])
+    xs = tuple(xs)
+    x = (ctypes.c_double * 3)(*((xs[0], 0.0, xs[1]) if len(xs) == 2 else xs))
+    _check(h, load().egb_zmarch(h, medium, x, len(omegas), om, float(beam_width), int(n_theta),
+                                 float(theta_max), float(cfl), _ptr(u_out), _ptr(count), _ptr(T),
+                                 _ptr(A), kmax))
 
 
 def egb_sync(h):
@@ -284,6 +297,18 @@ class Context:
         egb_release(self.h, s)
         egb_release(self.h, m)
         return res, info
+
+    def zmarch(self, medium, problem, n_theta, theta_max, cfl=0.5, kmax=8):
+        """Depth march of a 2-D problem's source on `medium` (both branches); returns the outputs
+        (u (n_omega, nz, nx), count, T, A) like superpose."""
+        nz, nx = problem.nz, problem.nx
+        u = np.zeros((len(problem.freqs), nz, nx), np.complex64)
+        cnt = np.zeros((nz, nx), np.uint8)
+        T = np.zeros((nz, nx, kmax), np.float64)
+        A = np.zeros((nz, nx, kmax), np.float32)
+        egb_zmarch(self.h, medium, problem.xs, problem.omegas, problem.beam_width, n_theta, theta_max,
+                   cfl, u, cnt, T, A, kmax)
+        return SolveResult(u, cnt, T, A)
 
     def solve_problem(self, problem, steps=None, kmax=8):
         """medium -> source -> evolve -> superpose for one 2-D problem; returns (result, info)."""

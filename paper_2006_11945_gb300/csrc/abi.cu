@@ -102,6 +102,7 @@ egb_status latched(egb_ctx *c) {
         if (bits & DeviceErrors::TIMEOUT) return fail(c, EGB_E_TIMEOUT, "bounded device wait expired");
         if (bits & DeviceErrors::NUMERIC) return fail(c, EGB_E_NUMERIC, "non-finite value produced");
         if (bits & DeviceErrors::OVERFLOW) return fail(c, EGB_E_ARRIVAL_OVERFLOW, "more arrivals or beam centres than the capacity");
+        if (bits & DeviceErrors::PARAXIAL) return fail(c, EGB_E_INVALID, "rays of a depth-march branch turn horizontal (Vz changes sign): lower theta_max");
     }
     return EGB_OK;
 }
@@ -659,6 +660,81 @@ egb_status egb_superpose_noalloc(egb_ctx *c, egb_solve_id sid, void *u_out, uint
     s->scratch_bytes = own_bytes;
     if (e != cudaSuccess) return cuda_fail(c, e, "superpose (fixed scratch)");
     return EGB_OK;
+}
+
+egb_status egb_zmarch(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_omega, const double *omega,
+                      double beam_width, int n_theta, double theta_max, double cfl, void *u_out,
+                      uint8_t *count, double *T, float *A, int kmax) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->media.find(mid);
+    if (it == c->media.end()) return fail(c, EGB_E_INVALID, "unknown medium id");
+    Medium *m = it->second;
+    if (m->dim != 2) return fail(c, EGB_E_INVALID, "the depth march takes 2-D media");
+    if (!xs) return fail(c, EGB_E_INVALID, "null source");
+    if (n_omega < 0 || n_omega > 64 || (n_omega > 0 && !omega)) return fail(c, EGB_E_INVALID, "n_omega must be in 0..64");
+    for (int i = 0; i < n_omega; ++i)
+        if (!(omega[i] > 0)) return fail(c, EGB_E_INVALID, "omega must be > 0");
+    if (u_out && n_omega == 0) return fail(c, EGB_E_INVALID, "u_out given without frequencies");
+    if (!(beam_width > 0)) return fail(c, EGB_E_INVALID, "beam width must be > 0");
+    if (n_theta < 4 || n_theta > 4096) return fail(c, EGB_E_INVALID, "n_theta must be in 4..4096");
+    if (!(theta_max > 0 && theta_max < 0.5 * M_PI)) return fail(c, EGB_E_INVALID, "theta_max must be in (0, pi/2)");
+    if (!(cfl > 0 && cfl <= 1.0)) return fail(c, EGB_E_INVALID, "cfl must be in (0, 1]");
+    bool want_arr = count || T || A;
+    if (want_arr && (kmax < 1 || kmax > 32)) return fail(c, EGB_E_INVALID, "kmax must be in 1..32");
+    if (m->nx < 4 || m->nz < 2) return fail(c, EGB_E_INVALID, "the depth march needs nx >= 4 and nz >= 2");
+    double fz = (xs[2] - m->oz) / m->hz;
+    int js = (int)std::lround(fz);
+    if (!(std::fabs(fz - js) <= 1e-6) || js < 0 || js >= m->nz)
+        return fail(c, EGB_E_INVALID, "the source depth must lie on a grid row");
+    if (!(xs[0] >= m->ox && xs[0] <= m->ox + (m->nx - 1) * m->hx)) return fail(c, EGB_E_INVALID, "source outside the grid");
+    DeviceGuard dg(c->device);
+    egb_status pre = latched(c);  // medium validation result
+    if (pre != EGB_OK) return pre;
+    ZmParams P;
+    P.xs = xs[0];
+    P.zs = m->oz + js * m->hz;
+    P.js = js;
+    P.n_theta = n_theta;
+    P.theta_max = theta_max;
+    P.cfl = cfl;
+    P.w0 = beam_width;
+    P.n_omega = n_omega;
+    size_t nodes = (size_t)m->nx * m->nz;
+    size_t ub = (size_t)n_omega * nodes * 8;
+    size_t need = zmarch_device_bytes(P, m->nx, m->nz) + ub + nodes * (1 + 12 * (size_t)kmax);
+    if (need > free_bytes()) return fail(c, EGB_E_NOMEM, "depth march needs %zu bytes", need);
+    cudaError_t e = cudaSuccess;
+    double *om = nullptr;
+    void *du = u_out;
+    uint8_t *dc = count;
+    double *dT = T;
+    float *dA = A;
+    bool hu = u_out && !is_device_ptr(u_out), hc = count && !is_device_ptr(count);
+    bool hT = T && !is_device_ptr(T), hA = A && !is_device_ptr(A);
+    if (n_omega > 0) e = cudaMalloc(&om, (size_t)n_omega * 8);
+    if (e == cudaSuccess && n_omega > 0) e = cudaMemcpyAsync(om, omega, (size_t)n_omega * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && hu) e = cudaMalloc(&du, ub);
+    if (e == cudaSuccess && hc) e = cudaMalloc(&dc, nodes);
+    if (e == cudaSuccess && hT) e = cudaMalloc(&dT, nodes * kmax * 8);
+    if (e == cudaSuccess && hA) e = cudaMalloc(&dA, nodes * kmax * 4);
+    if (e == cudaSuccess && du) e = cudaMemsetAsync(du, 0, ub, c->stream);
+    if (e == cudaSuccess) e = zmarch_run(*m, P, om, (float2 *)du, dc, dT, dA, kmax, c->d_err, c->stream);
+    if (e == cudaSuccess && hu) e = cudaMemcpyAsync(u_out, du, ub, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hc) e = cudaMemcpyAsync(count, dc, nodes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hT) e = cudaMemcpyAsync(T, dT, nodes * kmax * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hA) e = cudaMemcpyAsync(A, dA, nodes * kmax * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (hu) cudaFree(du);
+    if (hc) cudaFree(dc);
+    if (hT) cudaFree(dT);
+    if (hA) cudaFree(dA);
+    cudaFree(om);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(c, EGB_E_NOMEM, "depth march buffers") : cuda_fail(c, e, "depth march");
+    }
+    return latched(c);
 }
 
 egb_status egb_sync(egb_ctx *c) {

@@ -78,7 +78,7 @@ __device__ __forceinline__ ff ff_add_f(float hi, float lo, float d) {
 }
 
 struct DeviceErrors {  // bits latched by kernels, read by egb_sync
-    enum : unsigned { NOT_PD = 1u, NUMERIC = 2u, OVERFLOW = 4u, TIMEOUT = 8u };
+    enum : unsigned { NOT_PD = 1u, NUMERIC = 2u, OVERFLOW = 4u, TIMEOUT = 8u, PARAXIAL = 16u };
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -238,5 +238,19 @@ size_t superpose3d_scratch_bytes(const Solve3D &sv);
 cudaError_t launch_superpose3d(Solve3D &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                                float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 cudaError_t launch_read_state3d(const Solve3D &sv, double *out_dev, cudaStream_t s);
+
+// Paraxial depth march (zmarch.cu): both branches from the source row and their superposition.
+struct ZmParams {
+    double xs, zs;      // source position (zs on grid row js)
+    int js;
+    int n_theta;        // angles per branch
+    double theta_max;   // half-width of the angle range (rad)
+    double cfl;
+    double w0;          // beam width (m)
+    int n_omega;
+};
+size_t zmarch_device_bytes(const ZmParams &P, int nx, int nz);
+cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_dev, float2 *u,
+                       uint8_t *count, double *T, float *A, int kmax, unsigned *d_err, cudaStream_t s);
 
 }  // namespace egb

@@ -1,0 +1,157 @@
+"""Parity of the CUDA depth march (egb_zmarch: Eqs. 13-20 with the same-row superposition of
+Eqs. 25-28, 33-35) with the FP64 oracle, through the C ABI.
+
+Bar (as for the pseudo-time path): wavefield relative L2 <= 2e-3, arrival counts exact outside the
+nodes whose count hinges on a sign of X - x_s below 2e-4 h, traveltimes <= 1e-5 and amplitudes
+<= 1e-3 relative where the counts agree.  Cases: homogeneous VTI, heterogeneous TTI, a focusing lens
+(triplicated arrivals), a ragged grid with the source off the centre column, sources on the top
+row (no upgoing branch), on the bottom row (no march downward) and one row below the top; invalid
+arguments; a medium where a branch's rays turn horizontal.  Full size (the timed workload's
+512 x 512 grid, 256 angles per branch, 5 m): homogeneous VTI against the closed-form traveltimes
+and geometrical amplitudes of straight group rays at every node of the central cone.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import synthmedia
+from oracle import closed_forms as CF
+from oracle import zmarch as ZM
+from tests.test_oracle_zmarch import lens_problem
+
+pytestmark = pytest.mark.gpu
+
+THETA_MAX = math.radians(60.0)
+
+
+def _gpu(p, nth, theta_max=THETA_MAX, kmax=8):
+    import paper_2006_11945_gb300 as egb
+    with egb.Context(0) as ctx:
+        m = ctx.medium_2d(p)
+        return ctx.zmarch(m, p, nth, theta_max, 0.5, kmax)
+
+
+def _compare(res, ref, p, parts):
+    out = {}
+    u, ur = res.u.astype(np.complex128), ref['u']
+    out['u_rel_l2'] = float(np.linalg.norm(u - ur) / np.linalg.norm(ur))
+    amb = ZM.ambiguous_nodes(p, parts, 2e-4 * max(p.hx, p.hz))
+    ok = ~amb
+    out['count_mismatch'] = int(np.sum((res.count != ref['count']) & ok))
+    same = (res.count == ref['count']) & ok
+    kk = np.arange(res.T.shape[-1])[None, None, :] < ref['count'][..., None]
+    sel = same[..., None] & kk
+    Tr, Ar = ref['T'][sel], ref['A'][sel]
+    out['T_rel_max'] = float(np.max(np.abs(res.T[sel] - Tr) / Tr)) if sel.any() else 0.0
+    out['A_rel_max'] = float(np.max(np.abs(res.A[sel] - Ar) / Ar)) if sel.any() else 0.0
+    out['arrivals'] = int(sel.sum())
+    out['ambiguous'] = int(amb.sum())
+    return out
+
+
+def _ragged():
+    """The first 41 rows and 53 columns of the 64 x 64 TTI medium, source at (25 h + 3.7 m, 17 h)."""
+    full = synthmedia.tti_heterogeneous(n=64, n_theta=64, length=2560.0, steps=1, freqs=(10.0,))
+    c21 = np.asarray(full.c21).reshape(64, 64, 21)[:41, :53].reshape(-1, 21).copy()
+    rho = np.asarray(full.rho).reshape(64, 64)[:41, :53].reshape(-1).copy()
+    return dataclasses.replace(full, nx=53, nz=41, c21=c21, rho=rho,
+                               xs=(25 * full.hx + 3.7, 17 * full.hz))
+
+
+def _case(name):
+    if name == 'vti48':
+        return synthmedia.vti_homogeneous(n=48, n_theta=32, steps=1, freqs=(15.0, 30.0)), 32
+    if name == 'tti64':
+        return synthmedia.tti_heterogeneous(n=64, n_theta=64, length=2560.0, steps=1, freqs=(10.0, 20.0)), 64
+    if name == 'lens64':
+        return lens_problem(), 96
+    return _ragged(), 48
+
+
+@pytest.mark.parametrize('name', ['vti48', 'tti64', 'lens64', 'ragged'])
+def test_zmarch_matches_the_oracle(name):
+    p, nth = _case(name)
+    res = _gpu(p, nth)
+    ref = ZM.solve(p, nth, THETA_MAX, 0.5)
+    m = _compare(res, ref, p, ref['parts'])
+    print(name, m)
+    assert m['u_rel_l2'] < 2e-3, m
+    assert m['count_mismatch'] == 0 and m['arrivals'] > 100, m
+    assert m['T_rel_max'] < 1e-5 and m['A_rel_max'] < 1e-3, m
+    if name == 'lens64':
+        assert res.count.max() == 3
+
+
+@pytest.mark.parametrize('row', [0, 1, 47])
+def test_zmarch_sources_on_the_edge_rows(row):
+    p = synthmedia.vti_homogeneous(n=48, n_theta=32, steps=1, freqs=(20.0,))
+    p = dataclasses.replace(p, xs=(200.0 + 3.3, row * p.hz))
+    res = _gpu(p, 32)
+    ref = ZM.solve(p, 32, THETA_MAX, 0.5)
+    m = _compare(res, ref, p, ref['parts'])
+    print(row, m)
+    assert m['u_rel_l2'] < 2e-3 and m['count_mismatch'] == 0, m
+    assert m['T_rel_max'] < 1e-5 and m['A_rel_max'] < 1e-3, m
+
+
+def test_zmarch_rejects_invalid_arguments_and_turning_rays():
+    import paper_2006_11945_gb300 as egb
+    p = synthmedia.tti_heterogeneous(n=32, n_theta=16, length=1280.0, steps=1, freqs=(10.0,))
+    q = synthmedia.vti_homogeneous_3d(n=8, n_theta=4, n_phi=8)
+
+    def status(fn):
+        try:
+            fn()
+        except egb.EgbError as e:
+            return e.status
+        return egb.EGB_OK
+
+    with egb.Context(0) as ctx:
+        m = ctx.medium_2d(p)
+        u = np.zeros((1, p.nz, p.nx), np.complex64)
+        call = lambda xs=p.xs, nth=16, tm=1.0, cfl=0.5, mm=m: egb.egb_zmarch(
+            ctx.h, mm, xs, p.omegas, 50.0, nth, tm, cfl, u_out=u)
+        assert status(call) == egb.EGB_OK
+        assert status(lambda: call(xs=(p.xs[0], p.xs[1] + 0.3 * p.hz))) == egb.EGB_E_INVALID
+        assert status(lambda: call(xs=(-5.0, p.xs[1]))) == egb.EGB_E_INVALID
+        assert status(lambda: call(nth=3)) == egb.EGB_E_INVALID
+        assert status(lambda: call(tm=math.pi / 2)) == egb.EGB_E_INVALID
+        assert status(lambda: call(cfl=1.5)) == egb.EGB_E_INVALID
+        m3 = ctx.medium_3d(q)
+        assert status(lambda: call(mm=m3)) == egb.EGB_E_INVALID
+        # phase angles up to 1.55 rad: some group directions in the tilted medium cross the horizontal
+        assert status(lambda: call(tm=1.55)) == egb.EGB_E_INVALID
+        assert status(call) == egb.EGB_OK        # the context stays usable
+
+
+def test_zmarch_full_size_homogeneous_vti_against_straight_rays():
+    """The timed workload's grid and angle sampling (512 x 512 at 5 m, 256 angles per branch,
+    theta_max 60 deg, source at the centre) in a homogeneous VTI medium: one arrival per node of
+    the cone |group angle| < 45 deg beyond 20 m, with T = r / |V_g| and A = |u_GO| sqrt(omega) of
+    the closed-form far field."""
+    p = synthmedia.vti_homogeneous(n=512, h=5.0, n_theta=256, steps=1, freqs=(20.0,))
+    res = _gpu(p, 256)
+    m_ = p.meta
+    x = np.arange(p.nx) * p.hx - p.xs[0]
+    z = np.arange(p.nz) * p.hz - p.xs[1]
+    Zg, Xg = np.meshgrid(z, x, indexing='ij')
+    r = np.hypot(Xg, Zg)
+    ang = np.degrees(np.arctan2(np.abs(Xg), np.abs(Zg)))
+    sel = (ang < 45) & (r > 20.0)
+    rng = np.random.default_rng(5)
+    idx = np.flatnonzero(sel)
+    pick = rng.choice(idx, size=4000, replace=False)
+    iz, ix = np.unravel_index(pick, sel.shape)
+    assert np.all(res.count[sel] == 1)
+    om = 2 * math.pi * 20.0
+    v_of = lambda th: CF.thomsen_vti_phase_velocity(th, m_['vp0'], m_['vs0'], m_['eps'], m_['delta'])
+    V_of = lambda th: CF.vti_group_velocity(th, m_['vp0'], m_['vs0'], m_['eps'], m_['delta'])[1:]
+    ref, T, _ = CF.homogeneous_go_green(Xg[iz, ix], Zg[iz, ix], 0.0, 0.0, om, v_of, V_of, m_['vp0'])
+    eT = np.abs(res.T[iz, ix, 0] - T) / T
+    Aref = np.abs(ref) * math.sqrt(om)
+    eA = np.abs(res.A[iz, ix, 0] - Aref) / Aref
+    print('full-size z-march VTI: T rel max', eT.max(), 'A rel max', eA.max())
+    assert eT.max() < 2e-4 and eA.max() < 2e-3
+    assert np.all(np.isfinite(res.u))
