@@ -62,7 +62,7 @@ ALGO_BYTES_PER_CELL_UPDATE_3D = 92.0
 
 
 def workload(name):
-    if name == 'tti512':
+    if name in ('tti512', 'zmarch'):
         return synthmedia.tti_heterogeneous(n=512, h=5.0, n_theta=256, freqs=(10.0, 20.0, 40.0))
     if name == 'vti64':
         return synthmedia.vti_homogeneous()
@@ -459,6 +459,120 @@ def fp64_form(p, steps, device):
             'note': 'plain FP64 stencil, one thread per cell, evolution only'}
 
 
+# Depth march (--workload zmarch): per (theta, x) cell and stage launch the four state fields are
+# read (16 B) and written (16 B), u^n is read in stages 2 and 3 (16 B) and the coefficients U, W, S of
+# the two bounding rows are read (24 B): (56 + 72 + 72) / 3 B per cell and launch.
+ALGO_BYTES_PER_CELL_STAGE_ZM = (56.0 + 72.0 + 72.0) / 3.0
+
+
+def run_zmarch(args):
+    """The paper's paraxial depth march (egb_zmarch) on the 512 x 512 TTI medium: whole solves
+    (medium upload, both branches, 3-frequency superposition and arrivals) through the C ABI."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    torch.cuda.set_device(0)
+    p = workload('zmarch')
+    if args.zm_n != 512:  # a smaller grid of the same physical extent (profiling captures)
+        p = synthmedia.tti_heterogeneous(n=args.zm_n, h=2560.0 / args.zm_n, n_theta=256,
+                                         freqs=(10.0, 20.0, 40.0))
+    nth, tmax = args.zm_theta, math.radians(args.zm_theta_max)
+    stream = torch.cuda.Stream()
+    ctx = egb.Context(0, stream.cuda_stream)
+    c21_d = torch.from_numpy(np.ascontiguousarray(p.c21)).cuda()
+    rho_d = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    c21_h = torch.from_numpy(np.ascontiguousarray(p.c21)).pin_memory()
+    rho_h = torch.from_numpy(np.ascontiguousarray(p.rho)).pin_memory()
+    no, kmax = len(p.freqs), 8
+    outs_d = (torch.empty((no, p.nz, p.nx, 2), dtype=torch.float32, device='cuda'),
+              torch.empty((p.nz, p.nx), dtype=torch.uint8, device='cuda'),
+              torch.empty((p.nz, p.nx, kmax), dtype=torch.float64, device='cuda'),
+              torch.empty((p.nz, p.nx, kmax), dtype=torch.float32, device='cuda'))
+    outs_h = tuple(torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs_d)
+    infos = []
+
+    def solve(host):
+        c21, rho = (c21_h, rho_h) if host else (c21_d, rho_d)
+        m = egb.egb_medium(ctx.h, (p.nx, 1, p.nz), (p.hx, 1.0, p.hz), (p.origin[0], 0.0, p.origin[1]), c21, rho)
+        u, cnt, T, A = outs_h if host else outs_d
+        info = egb.egb_zmarch(ctx.h, m, p.xs, p.omegas, p.beam_width, nth, tmax, p.cfl, u, cnt, T, A, kmax)
+        egb.egb_release(ctx.h, m)
+        infos.append(info)
+        return info
+
+    def timed(host, K, W):
+        for _ in range(W):
+            solve(host)
+        infos.clear()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+        for _ in range(K):
+            info = solve(host)
+        with torch.cuda.stream(stream):
+            t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1), info
+
+    with ClockSampler(0) as clk:
+        ms, info = timed(False, args.steps, args.warmup)
+    march_ms = float(np.mean([i['march_ms'] for i in infos]))
+    setup_ms = float(np.mean([i['setup_ms'] for i in infos]))
+    sup_ms = float(np.mean([i['superpose_ms'] for i in infos]))
+    e2e_ms, _ = timed(True, max(1, args.steps), 1)
+    cu = info['cell_updates']
+    launch_ms = march_ms / info['stage_launches']
+    achieved = ALGO_BYTES_PER_CELL_STAGE_ZM * nth * p.nx / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    h2d = p.c21.nbytes + p.rho.nbytes
+    d2h = sum(o.numel() * o.element_size() for o in outs_h)
+    line = {
+        'metric': 'phase-space cell-updates/s', 'value': cu * args.steps / (ms / 1e3),
+        'unit': 'cell-updates/s', 'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup,
+        'ms_per_step': ms / args.steps, 'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': 'f32 (double-float tau and phase)', 'data': 'synthetic (seeded TTI medium)',
+        'config': {'workload': f'paraxial depth march (Eqs. 13-20), {p.name} {p.nx}x{p.nz} at {p.hx:g} m, '
+                               f'{nth} angles per branch within +-{args.zm_theta_max:g} deg, both branches, '
+                               f'{len(p.freqs)} frequencies', 'cells_per_row': nth * p.nx,
+                   'n_sub': info['n_sub'], 'rows': info['rows'], 'freqs_hz': p.freqs,
+                   'l2': 'per-row state (2 MB) L2-resident; coefficient and history volumes (1.9 GB) larger than L2, no flush'},
+        'solves_per_s': args.steps / (ms / 1e3),
+        'phase_ms': {'setup': setup_ms, 'march': march_ms, 'superpose': sup_ms},
+        'e2e': {'value': cu * max(1, args.steps) / (e2e_ms / 1e3), 'unit': 'cell-updates/s',
+                'h2d_bytes_per_step': int(h2d), 'd2h_bytes_per_step': int(d2h)},
+        'roofline': {'bound': 'hbm', 'kernel': 'k_zm_stage', 'achieved': achieved, 'peak': peak, 'unit': 'GB/s',
+                     'frac': achieved / peak, 'traffic': None, 'peak_kind': peak_kind, 'launch_ms': launch_ms},
+        'gpu_launches': (2 + info['kernel_launches']) * args.steps,
+        'clocks': clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line['cpu_baseline'] = cpu_baseline_zmarch(p, args.cpu_seconds)
+    print(json.dumps(line))
+    ctx.close()
+
+
+def _zmarch_sample(p):
+    """128 x 128 sub-block of the workload medium with 64 angles per branch (downgoing branch)."""
+    from oracle import zmarch as ZM
+    q = _oracle_sample(p, 128)
+    return q, ZM.ZSetup(q, 64, math.radians(60.0), 1, q.cfl)
+
+
+def cpu_baseline_zmarch(p, budget_s=20.0):
+    """Time the FP64 oracle's depth march (downgoing branch, setup excluded) on a bounded sample."""
+    from oracle import zmarch as ZM
+    q, Z = _zmarch_sample(p)
+    t = time.perf_counter()
+    ZM.march(Z)
+    el = time.perf_counter() - t
+    cu = (len(Z.rows) - 1) * Z.n_sub * Z.nth * Z.nx
+    cores = int(os.environ.get('OMP_NUM_THREADS', os.cpu_count() or 1))
+    return {'value': cu / el, 'unit': 'cell-updates/s', 'cores': cores, 'kind': 'oracle',
+            'sample': f'{q.nx}x{q.nz} sub-block of the workload medium, 64 angles within +-60 deg, the '
+                      f'downgoing branch ({len(Z.rows)} rows x {Z.n_sub} substeps) of the float64 '
+                      f'oracle march, setup excluded ({el:.1f} s)'}
+
+
 def _oracle_sample(p, sub=128):
     """A sub-block of the workload's medium (same spacing and angle count) for the CPU oracle."""
     n = min(sub, p.nx)
@@ -494,6 +608,8 @@ def run_reference(args):
     if rank != 0:
         return
     p = workload(args.workload)
+    if args.workload == 'zmarch':
+        return run_reference_zmarch(args, p, ws)
     q = _oracle_sample(p)
     from oracle import liouville as OL
     S = OL.Setup(q)
@@ -514,6 +630,32 @@ def run_reference(args):
         'ms_per_step': el / args.steps * 1e3, 'higher_is_better': True, 'scaling': 'weak',
         'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded TTI medium)',
         'config': {'workload': f'{p.name} {p.nx}x{p.nz} at {p.hx:g} m x {p.n_theta} angles (oracle sample)'},
+        'cpu_baseline': {'value': value, 'unit': 'cell-updates/s', 'cores': cores, 'kind': 'oracle',
+                         'sample': sample},
+        'e2e': {'value': value, 'unit': 'cell-updates/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+    }))
+
+
+def run_reference_zmarch(args, p, ws):
+    """Reference arm of the depth-march workload: the FP64 oracle march on its bounded sample."""
+    from oracle import zmarch as ZM
+    q, Z = _zmarch_sample(p)
+    cu = (len(Z.rows) - 1) * Z.n_sub * Z.nth * Z.nx
+    for _ in range(args.warmup):
+        ZM.march(Z)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        ZM.march(Z)
+    el = time.perf_counter() - t
+    value = cu * args.steps / el
+    cores = int(os.environ.get('OMP_NUM_THREADS', os.cpu_count() or 1))
+    sample = f'{q.nx}x{q.nz} sub-block, 64 angles, downgoing branch of the float64 oracle march per step'
+    print(json.dumps({
+        'impl': 'reference', 'metric': 'phase-space cell-updates/s', 'value': value,
+        'unit': 'cell-updates/s', 'n_gpus': ws, 'steps': args.steps, 'warmup': args.warmup,
+        'ms_per_step': el / args.steps * 1e3, 'higher_is_better': True, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded TTI medium)',
+        'config': {'workload': f'paraxial depth march, {p.name} {p.nx}x{p.nz} (oracle sample)'},
         'cpu_baseline': {'value': value, 'unit': 'cell-updates/s', 'cores': cores, 'kind': 'oracle',
                          'sample': sample},
         'e2e': {'value': value, 'unit': 'cell-updates/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
@@ -576,7 +718,11 @@ def main():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
     ap.add_argument('--workload', default='tti512',
-                    choices=['tti512', 'tti256', 'tti128', 'vti64', 'tri96', 'tri48', 'batch', 'serve'])
+                    choices=['tti512', 'tti256', 'tti128', 'vti64', 'tri96', 'tri48', 'batch', 'serve',
+                             'zmarch'])
+    ap.add_argument('--zm-theta', type=int, default=256)
+    ap.add_argument('--zm-n', type=int, default=512)
+    ap.add_argument('--zm-theta-max', type=float, default=60.0)
     ap.add_argument('--batch-count', type=int, default=6)
     ap.add_argument('--serve-seconds', type=float, default=2.0)
     ap.add_argument('--serve-large-scale', type=float, default=1.0)
@@ -595,6 +741,8 @@ def main():
         run_egb3d(args)
     elif args.workload == 'batch':
         run_batch(args)
+    elif args.workload == 'zmarch':
+        run_zmarch(args)
     else:
         run_egb(args)
 

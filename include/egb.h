@@ -223,12 +223,26 @@ egb_status egb_read_velocity(egb_ctx *ctx, egb_solve_id solve, float *out);
  *   count, T, A   arrivals per node ([nz][nx] uint8, [nz][nx][kmax] float64 s, float32), each may
  *              be NULL; kmax in 1..32 when any is given; more arrivals than kmax give
  *              EGB_E_ARRIVAL_OVERFLOW after the earliest kmax are written
+ *   info       optional (NULL allowed): facts about the run for callers that report throughput,
+ *              not a step of the method (see egb_zmarch_info)
  * Synchronous: returns when the outputs are written.  The work buffers (about 44 bytes per
  * phase-space cell of the larger branch) are allocated and freed by the call; EGB_E_NOMEM when
  * they do not fit. */
+typedef struct {
+    int n_sub[2];             /* TVD-RK3 substeps per row interval: [0] downgoing, [1] upgoing (0: absent) */
+    int rows[2];              /* rows of each branch, the source row included */
+    uint64_t cell_updates;    /* (theta, x) cells advanced one full substep, both branches */
+    uint64_t stage_launches;  /* stage kernel launches (3 per substep) */
+    uint64_t kernel_launches; /* every kernel the call launched */
+    double setup_ms;          /* device time of the characteristic tables (CUDA events, ctx stream) */
+    double march_ms;          /* device time of the depth march (initial data and stages) */
+    double superpose_ms;      /* device time of the beams and arrivals */
+} egb_zmarch_info;
+
 egb_status egb_zmarch(egb_ctx *ctx, egb_medium_id medium, const double xs[3], int n_omega,
                       const double *omega, double beam_width_m, int n_theta, double theta_max,
-                      double cfl, void *u_out, uint8_t *count, double *T, float *A, int kmax);
+                      double cfl, void *u_out, uint8_t *count, double *T, float *A, int kmax,
+                      egb_zmarch_info *info);
 
 #ifdef __cplusplus
 }

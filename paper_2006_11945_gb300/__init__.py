@@ -42,6 +42,12 @@ class egb_opts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int), ('store_velocity', ctypes.c_int), ('checked', ctypes.c_int)]
 
 
+class egb_zmarch_info(ctypes.Structure):
+    _fields_ = [('n_sub', ctypes.c_int * 2), ('rows', ctypes.c_int * 2), ('cell_updates', ctypes.c_uint64),
+                ('stage_launches', ctypes.c_uint64), ('kernel_launches', ctypes.c_uint64),
+                ('setup_ms', ctypes.c_double), ('march_ms', ctypes.c_double), ('superpose_ms', ctypes.c_double)]
+
+
 class egb_solve_info(ctypes.Structure):
     _fields_ = [('nx', ctypes.c_int), ('nz', ctypes.c_int), ('n_theta', ctypes.c_int),
                 ('n_omega', ctypes.c_int), ('steps_done', ctypes.c_int), ('dt', ctypes.c_double),
@@ -81,7 +87,7 @@ def load(path: Optional[str] = None):
     lib.egb_get_solve_info.argtypes = [vp, u64, P(egb_solve_info)]
     lib.egb_read_state.argtypes = [vp, u64, vp]
     lib.egb_read_velocity.argtypes = [vp, u64, vp]
-    lib.egb_zmarch.argtypes = [vp, u64, P(d), i, P(d), d, i, d, d, vp, vp, vp, vp, i]
+    lib.egb_zmarch.argtypes = [vp, u64, P(d), i, P(d), d, i, d, d, vp, vp, vp, vp, i, P(egb_zmarch_info)]
     for name in EXPORTED:
         if name != 'egb_last_error':
             getattr(lib, name).restype = i
@@ -169,13 +175,17 @@ def egb_superpose_noalloc(h, solve, u_out=None, count=None, T=None, A=None, kmax
 def egb_zmarch(h, medium, xs, omegas, beam_width, n_theta, theta_max, cfl=0.5, u_out=None, count=None,
                T=None, A=None, kmax=8):
     """The paper's paraxial depth march from the source row, both branches, with its same-row
-    superposition (see include/egb.h)."""
+    superposition (see include/egb.h).  Returns the run's egb_zmarch_info as a dict."""
     om = (ctypes.c_double * max(len(omegas), 1))(*[float(w) for w in omegas])
     xs = tuple(xs)
     x = (ctypes.c_double * 3)(*((xs[0], 0.0, xs[1]) if len(xs) == 2 else xs))
+    info = egb_zmarch_info()
     _check(h, load().egb_zmarch(h, medium, x, len(omegas), om, float(beam_width), int(n_theta),
                                  float(theta_max), float(cfl), _ptr(u_out), _ptr(count), _ptr(T),
-                                 _ptr(A), kmax))
+                                 _ptr(A), kmax, ctypes.byref(info)))
+    out = {k: getattr(info, k) for k, _ in egb_zmarch_info._fields_}
+    out['n_sub'], out['rows'] = list(info.n_sub), list(info.rows)
+    return out
 
 
 def egb_sync(h):

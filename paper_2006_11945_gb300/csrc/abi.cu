@@ -664,7 +664,7 @@ egb_status egb_superpose_noalloc(egb_ctx *c, egb_solve_id sid, void *u_out, uint
 
 egb_status egb_zmarch(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_omega, const double *omega,
                       double beam_width, int n_theta, double theta_max, double cfl, void *u_out,
-                      uint8_t *count, double *T, float *A, int kmax) {
+                      uint8_t *count, double *T, float *A, int kmax, egb_zmarch_info *info) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->media.find(mid);
@@ -719,7 +719,7 @@ egb_status egb_zmarch(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     if (e == cudaSuccess && hT) e = cudaMalloc(&dT, nodes * kmax * 8);
     if (e == cudaSuccess && hA) e = cudaMalloc(&dA, nodes * kmax * 4);
     if (e == cudaSuccess && du) e = cudaMemsetAsync(du, 0, ub, c->stream);
-    if (e == cudaSuccess) e = zmarch_run(*m, P, om, (float2 *)du, dc, dT, dA, kmax, c->d_err, c->stream);
+    if (e == cudaSuccess) e = zmarch_run(*m, P, om, (float2 *)du, dc, dT, dA, kmax, c->d_err, c->stream, info);
     if (e == cudaSuccess && hu) e = cudaMemcpyAsync(u_out, du, ub, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && hc) e = cudaMemcpyAsync(count, dc, nodes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && hT) e = cudaMemcpyAsync(T, dT, nodes * kmax * 8, cudaMemcpyDeviceToHost, c->stream);

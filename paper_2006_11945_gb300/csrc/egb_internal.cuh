@@ -251,6 +251,7 @@ struct ZmParams {
 };
 size_t zmarch_device_bytes(const ZmParams &P, int nx, int nz);
 cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_dev, float2 *u,
-                       uint8_t *count, double *T, float *A, int kmax, unsigned *d_err, cudaStream_t s);
+                       uint8_t *count, double *T, float *A, int kmax, unsigned *d_err, cudaStream_t s,
+                       egb_zmarch_info *info);
 
 }  // namespace egb

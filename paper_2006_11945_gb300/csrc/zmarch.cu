@@ -26,6 +26,7 @@
 //                 of every arrival (late arrivals included)
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "christoffel.cuh"
 
@@ -480,9 +481,19 @@ size_t zmarch_device_bytes(const ZmParams &P, int nx, int nz) {
 // d_err.  Synchronises s once per branch (to size the substeps from the largest CFL rate).
 cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_dev, float2 *u,
                        uint8_t *count, double *T, float *Aout, int kmax, unsigned *d_err,
-                       cudaStream_t st) {
+                       cudaStream_t st, egb_zmarch_info *info) {
     const int nx = m.nx, nz = m.nz, nth = P.n_theta;
     cudaError_t e = cudaSuccess;
+    egb_zmarch_info stats;
+    memset(&stats, 0, sizeof stats);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    auto lap = [&](int a, int b) {
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[a], ev[b]);
+        return (double)ms;
+    };
     float *src = nullptr, *rate = nullptr;
     float2 *sc = nullptr;
     double *theta = nullptr;
@@ -500,6 +511,7 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
     float c_ref = 0.f;  // source phase velocity along +z (scales the tau WENO epsilon)
     if (e == cudaSuccess) {
         zm::k_zm_source<<<1, 32, 0, st>>>(m, P.xs, P.zs, src);
+        stats.kernel_launches += 1;
         e = cudaMemcpyAsync(&c_ref, src + 22, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess && !(c_ref > 0.f)) c_ref = 1.f;  // non-PD medium: reported by the caller
@@ -537,8 +549,10 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         float4 *dat = (float4 *)alloc((size_t)P.n_omega * nr * nth * KC * 16 + 16);
         if (e != cudaSuccess) break;
         e = cudaMemsetAsync(rate, 0, 4, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
         if (e != cudaSuccess) break;
         k_zm_coef<<<dim3((nx + 127) / 128, nr), 128, 0, st>>>(m, G, sc, C, V, rate, d_err);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         float hrate = 0.f;
         e = cudaMemcpyAsync(&hrate, rate, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -546,6 +560,14 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         int n_sub = (int)std::ceil(m.hz * (double)hrate / P.cfl);
         if (!(n_sub >= 1)) n_sub = 1;
         if (n_sub > 4096) n_sub = 4096;  // a branch flagged invalid still terminates
+        const int bi = s > 0 ? 0 : 1;
+        stats.n_sub[bi] = n_sub;
+        stats.rows[bi] = nr;
+        stats.cell_updates += (uint64_t)(nr - 1) * n_sub * nth * nx;
+        stats.stage_launches += (uint64_t)3 * (nr - 1) * n_sub;
+        stats.kernel_launches += 2 + (uint64_t)3 * (nr - 1) * n_sub;
+        stats.setup_ms += lap(0, 1);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         const int64_t hk = (int64_t)nr * nx;  // history floats per angle
         dim3 pg((nx + 127) / 128, nth);
         k_zm_init<<<pg, 128, 0, st>>>(G, sc, theta, S0, H, T3, hk);
@@ -579,6 +601,7 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
             }
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
         if (e != cudaSuccess) break;
         SupArgsZ Z;
         Z.G = G;
@@ -602,17 +625,26 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         if (u && P.n_omega > 0) {
             k_zm_centres<<<(nr * nth + 127) / 128, 128, 0, st>>>(Z);
             k_zm_sum<<<dim3((nx + 127) / 128, nr - r_first), 128, 0, st>>>(Z, r_first, u, nz);
+            stats.kernel_launches += 2;
         }
-        if (count || T || Aout)
+        if (count || T || Aout) {
             k_zm_arrivals<<<dim3((nx + 127) / 128, nr - r_first), 128, 0, st>>>(Z, r_first, count, T, Aout, kmax);
+            stats.kernel_launches += 1;
+        }
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        stats.march_ms += lap(1, 2);
+        stats.superpose_ms += lap(2, 3);
         // this branch's buffers are done: free them before the next branch
         for (size_t q = 4; q < bufs.size(); ++q) cudaFree(bufs[q]);
         bufs.resize(4);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (void *p : bufs) cudaFree(p);
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (info) *info = stats;
     return e;
 }
 
