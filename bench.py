@@ -521,7 +521,7 @@ def run_zmarch(args):
     sup_ms = float(np.mean([i['superpose_ms'] for i in infos]))
     e2e_ms, _ = timed(True, max(1, args.steps), 1)
     cu = info['cell_updates']
-    launch_ms = march_ms / info['stage_launches']
+    launch_ms = march_ms / info['stage_passes']
     achieved = ALGO_BYTES_PER_CELL_STAGE_ZM * nth * p.nx / (launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     h2d = p.c21.nbytes + p.rho.nbytes

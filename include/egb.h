@@ -232,7 +232,8 @@ typedef struct {
     int n_sub[2];             /* TVD-RK3 substeps per row interval: [0] downgoing, [1] upgoing (0: absent) */
     int rows[2];              /* rows of each branch, the source row included */
     uint64_t cell_updates;    /* (theta, x) cells advanced one full substep, both branches */
-    uint64_t stage_launches;  /* stage kernel launches (3 per substep) */
+    uint64_t stage_passes;    /* stage kernel launches, each one pass over the (theta, x) plane
+                               * (3 per substep) */
     uint64_t kernel_launches; /* every kernel the call launched */
     double setup_ms;          /* device time of the characteristic tables (CUDA events, ctx stream) */
     double march_ms;          /* device time of the depth march (initial data and stages) */

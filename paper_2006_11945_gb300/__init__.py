@@ -44,7 +44,7 @@ class egb_opts(ctypes.Structure):
 
 class egb_zmarch_info(ctypes.Structure):
     _fields_ = [('n_sub', ctypes.c_int * 2), ('rows', ctypes.c_int * 2), ('cell_updates', ctypes.c_uint64),
-                ('stage_launches', ctypes.c_uint64), ('kernel_launches', ctypes.c_uint64),
+                ('stage_passes', ctypes.c_uint64), ('kernel_launches', ctypes.c_uint64),
                 ('setup_ms', ctypes.c_double), ('march_ms', ctypes.c_double), ('superpose_ms', ctypes.c_double)]
 
 

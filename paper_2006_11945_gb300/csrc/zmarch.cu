@@ -564,7 +564,7 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         stats.n_sub[bi] = n_sub;
         stats.rows[bi] = nr;
         stats.cell_updates += (uint64_t)(nr - 1) * n_sub * nth * nx;
-        stats.stage_launches += (uint64_t)3 * (nr - 1) * n_sub;
+        stats.stage_passes += (uint64_t)3 * (nr - 1) * n_sub;
         stats.kernel_launches += 2 + (uint64_t)3 * (nr - 1) * n_sub;
         stats.setup_ms += lap(0, 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
