@@ -155,3 +155,32 @@ def test_zmarch_full_size_homogeneous_vti_against_straight_rays():
     print('full-size z-march VTI: T rel max', eT.max(), 'A rel max', eA.max())
     assert eT.max() < 2e-4 and eA.max() < 2e-3
     assert np.all(np.isfinite(res.u))
+
+
+def test_full_size_tti_depth_march_agrees_with_the_pseudo_time_solve():
+    """The timed 512 x 512 TTI medium (256 angles): the pseudo-time solve (full angle range, 2801
+    steps) and the depth march (256 angles per branch within 60 deg) trace the same rays with
+    different numerics.  Below the source, within 30 deg of vertical and beyond 100 m, both must
+    see one arrival per node with the same traveltime and geometrical amplitude up to their
+    discretisation errors."""
+    import paper_2006_11945_gb300 as egb
+    p = synthmedia.tti_heterogeneous(n=512, h=5.0, n_theta=256, freqs=(10.0,))
+    with egb.Context(0) as ctx:
+        pt, _ = ctx.solve_problem(p)
+        m = ctx.medium_2d(p)
+        zm = ctx.zmarch(m, p, 256, THETA_MAX)
+    x = np.arange(p.nx) * p.hx - p.xs[0]
+    z = np.arange(p.nz) * p.hz - p.xs[1]
+    Zg, Xg = np.meshgrid(z, x, indexing='ij')
+    r = np.hypot(Xg, Zg)
+    ang = np.degrees(np.arctan2(np.abs(Xg), np.abs(Zg)))
+    sel = (ang < 30) & (r > 100.0) & (pt.count == 1)
+    assert sel.sum() > 20000
+    assert np.mean(zm.count[sel] == 1) > 0.999
+    both = sel & (zm.count == 1)
+    eT = np.abs(zm.T[..., 0][both] - pt.T[..., 0][both]) / pt.T[..., 0][both]
+    eA = np.abs(zm.A[..., 0][both] - pt.A[..., 0][both]) / pt.A[..., 0][both]
+    print('depth march vs pseudo-time, 512^2 TTI: nodes', int(both.sum()), 'T rel median / max',
+          np.median(eT), eT.max(), 'A rel median / q99', np.median(eA), np.quantile(eA, 0.99))
+    assert np.median(eT) < 2e-4 and eT.max() < 2e-3
+    assert np.median(eA) < 1e-2 and np.quantile(eA, 0.99) < 5e-2
