@@ -219,13 +219,20 @@ egb_status egb_read_velocity(egb_ctx *ctx, egb_solve_id solve, float *out);
  *   omega      n_omega angular frequencies (rad/s, > 0; host pointer), 0 <= n_omega <= 64
  *   beam_width_m  w0 > 0: initial transverse beam Hessian i 2 / (omega w0^2) (Eq. 24)
  *   n_theta    angles per branch, 4..4096; theta_max in (0, pi/2); cfl in (0, 1]
+ *   drt        dynamic ray tracing of the beams and arrival amplitudes: 0 from the gradients of
+ *              the labels at fixed depth; 1 advected with the march (Eq. 21, read anisotropically:
+ *              the ray perturbations (dx, dtheta) of the offset and take-off families obey
+ *              Q_z + u Q_x + w Q_theta = J Q, J the (x, theta) Jacobian of (dx/dz, dtheta/dz); about
+ *              36 more bytes per phase-space cell)
  *   u_out      complex64 [n_omega][nz][nx] (host or device), or NULL
  *   count, T, A   arrivals per node ([nz][nx] uint8, [nz][nx][kmax] float64 s, float32), each may
  *              be NULL; kmax in 1..32 when any is given; more arrivals than kmax give
  *              EGB_E_ARRIVAL_OVERFLOW after the earliest kmax are written
  *   info       optional (NULL allowed): facts about the run for callers that report throughput,
  *              not a step of the method (see egb_zmarch_info)
- * Synchronous: returns when the outputs are written.  The work buffers (about 44 bytes per
+ * Rays entering through the grid's x edges or the ends of the angle range carry no source-plane
+ * labels: an advected source indicator (ghost value 0) keeps them out of beams and arrivals.
+ * Synchronous: returns when the outputs are written.  The work buffers (about 48 bytes per
  * phase-space cell of the larger branch) are allocated and freed by the call; EGB_E_NOMEM when
  * they do not fit. */
 typedef struct {
@@ -242,8 +249,8 @@ typedef struct {
 
 egb_status egb_zmarch(egb_ctx *ctx, egb_medium_id medium, const double xs[3], int n_omega,
                       const double *omega, double beam_width_m, int n_theta, double theta_max,
-                      double cfl, void *u_out, uint8_t *count, double *T, float *A, int kmax,
-                      egb_zmarch_info *info);
+                      double cfl, int drt, void *u_out, uint8_t *count, double *T, float *A,
+                      int kmax, egb_zmarch_info *info);
 
 #ifdef __cplusplus
 }

@@ -27,12 +27,16 @@ Readings taken here:
 * Jiang & Peng's third-order HJ-WENO in x and theta, upwinded by the signs of U and W.  Two ghost
   cells on each side of x and of theta hold the linear extrapolation of the two outermost interior
   values (exact for fields linear in x or theta).
+* A source indicator q is advected like the labels from q = 1 on the source row, its ghosts hold
+  q = 0 (Dirichlet inflow): rays that enter through the x or theta boundaries carry no source-plane
+  data (their labels are extrapolations), and only cells with q > 1/2 take part in beam centres and
+  arrivals (the pseudo-time form's source indicator, for the same reason).
 * Rows j >= j_s of the output come from the downgoing branch, rows j < j_s from the upgoing one.
 
 Beams (same reading as the pseudo-time form's superposition, with the dynamic ray tracing taken
 from the label gradients in (x, theta) at fixed depth instead of advecting Eq. 21):
-* on each row and angle, every sign change of X - x_s between neighbouring nodes (sign(0) = +1) is
-  a beam centre; quantities are interpolated linearly there;
+* on each row and angle, every sign change of X - x_s between neighbouring nodes that both have
+  q > 1/2 (sign(0) = +1) is a beam centre; quantities are interpolated linearly there;
 * the perturbation (dx, dtheta) solves [[X_x, X_theta], [vartheta_x, vartheta_theta]] (dx, dtheta) =
   (1 / ghat_z, kappa), kappa = 2 i |V_s| / (omega w0^2), ghat_z and |V_s| the source medium's unit
   group direction and group speed at vartheta: at the source plane db/dX = ghat_z (b = (X - x_s)
@@ -44,7 +48,8 @@ from the label gradients in (x, theta) at fixed depth instead of advecting Eq. 2
 * weight i c_ref^2 / (4 pi v_s(vartheta)^2) times the take-off measure
   |d vartheta_c / d theta| dtheta = |vartheta_theta X_x - vartheta_x X_theta| / |X_x| dtheta (Eq. 33's
   Psi_0, calibrated as in the pseudo-time form);
-* arrivals at a node: sign changes of X - x_s between theta_k and theta_k+1, T = tau interpolated,
+* arrivals at a node: sign changes of X - x_s between theta_k and theta_k+1 (both q > 1/2), T = tau
+  interpolated,
   A = c_ref^2 sqrt(rho_s / rho_r) / (v_r sqrt(8 pi |V_s ghat_z| |X_theta|)) (|d_theta b| =
   |ghat_z X_theta| on Gamma), sorted by T then angle, at most kmax kept.
 """
@@ -60,7 +65,7 @@ from . import medium as _md
 GHOST = 2
 WENO_EPS_REL = 1e-6
 KMAH_ARG = 1e-3
-FIELDS = ('X', 'Th', 'tau')
+FIELDS = ('X', 'Th', 'tau', 'q')
 
 
 class ZSetup:
@@ -114,16 +119,21 @@ class ZSetup:
         self.n_sub = max(1, int(math.ceil(self.hz * self.max_rate / cfl)))
         h = max(self.hx, self.hz)
         self.eps = {'X': WENO_EPS_REL * h * h, 'Th': WENO_EPS_REL * self.dth ** 2,
-                    'tau': WENO_EPS_REL * (h / self.c_ref) ** 2}
+                    'tau': WENO_EPS_REL * (h / self.c_ref) ** 2, 'q': WENO_EPS_REL}
 
 
-def _pad(u):
+def _pad(u, dirichlet=None):
     """Two ghost cells per side in theta (axis 0) and x (axis 1) by linear extrapolation of the two
-    outermost interior values; the four corner blocks are never read and stay NaN."""
+    outermost interior values, or holding the value `dirichlet`; the four corner blocks are never
+    read and stay NaN."""
     nth, nx = u.shape
     G = GHOST
     p = np.full((nth + 2 * G, nx + 2 * G), np.nan)
     p[G:-G, G:-G] = u
+    if dirichlet is not None:
+        p[G:-G, :G] = p[G:-G, -G:] = dirichlet
+        p[:G, G:-G] = p[-G:, G:-G] = dirichlet
+        return p
     for k in (1, 2):
         p[G:-G, G - k] = (1 + k) * u[:, 0] - k * u[:, 1]
         p[G:-G, G + nx - 1 + k] = (1 + k) * u[:, -1] - k * u[:, -2]
@@ -150,7 +160,7 @@ def rhs(state, Z, U, W, S):
     G = GHOST
     nth, nx = Z.nth, Z.nx
     for f in FIELDS:
-        p = _pad(state[f])
+        p = _pad(state[f], 0.0 if f == 'q' else None)
         sx = {m: p[G:G + nth, G + m:G + m + nx] for m in range(-2, 3)}
         st = {m: p[G + m:G + m + nth, G:G + nx] for m in range(-2, 3)}
         dx = {j: sx[j + 1] - sx[j] for j in (-2, -1, 0, 1)}
@@ -170,7 +180,7 @@ def march(Z):
     nth, nx, nr = Z.nth, Z.nx, len(Z.rows)
     state = {'X': np.broadcast_to(Z.x[None, :], (nth, nx)).copy(),
              'Th': np.broadcast_to(Z.theta[:, None], (nth, nx)).copy(),
-             'tau': np.zeros((nth, nx))}
+             'tau': np.zeros((nth, nx)), 'q': np.ones((nth, nx))}
     hist = {f: np.empty((nth, nr, nx)) for f in FIELDS}
     for f in FIELDS:
         hist[f][:, 0] = state[f]
@@ -225,7 +235,8 @@ def green_rows(Z, H, omegas, beam_width, F=None):
     F = fields(Z, H) if F is None else F
     nth, nr, nx = F['X'].shape
     D = F['X'] - Z.xs[0]
-    cross = (D[..., :-1] >= 0) != (D[..., 1:] >= 0)
+    fl = H['q'] > 0.5  # rays carrying source-plane labels
+    cross = fl[..., :-1] & fl[..., 1:] & ((D[..., :-1] >= 0) != (D[..., 1:] >= 0))
     k, r, i = np.nonzero(cross)
     c0, c1 = (k, r, i), (k, r, i + 1)
     t = D[c0] / (D[c0] - D[c1])
@@ -274,7 +285,8 @@ def arrivals_rows(Z, H, kmax=8, F=None):
         Acell = Z.c_ref ** 2 * np.sqrt(Z.rho_s / rho_r) / (
             Z.vel['v'] * np.sqrt(8 * np.pi * np.abs(F['Vsn'] * F['gsz']) * np.abs(F['Xt'])))
     D = F['X'] - Z.xs[0]
-    cross = (D[:-1] >= 0) != (D[1:] >= 0)
+    fl = H['q'] > 0.5
+    cross = fl[:-1] & fl[1:] & ((D[:-1] >= 0) != (D[1:] >= 0))
     nth, nr, nx = D.shape
     ks, rs, ixs = np.nonzero(cross)
     t = D[ks, rs, ixs] / (D[ks, rs, ixs] - D[ks + 1, rs, ixs])
@@ -329,14 +341,19 @@ def solve(problem, n_theta, theta_max, cfl=0.5, kmax=8, omegas=None, beam_width=
     return dict(u=u, count=count, T=T, A=A, overflow=overflow, parts=parts)
 
 
-def ambiguous_nodes(problem, parts, tol):
-    """Nodes whose arrival count hinges on a sign of X - x_s below tol (m) at a counted crossing."""
+def ambiguous_nodes(problem, parts, tol, q_band=0.05):
+    """Nodes whose arrival count hinges on a decision below the rounding of an FP32 evaluation: a
+    sign change of X - x_s along theta with min |X - x_s| < tol (m), or with a source indicator
+    within q_band of the 1/2 threshold at either cell."""
     nz, nx = problem.nz, problem.nx
     amb = np.zeros((nz, nx), bool)
-    for s, (Z, H) in parts.items():
+    for s, part in parts.items():
+        Z, H = part[0], part[1]
         D = H['X'] - Z.xs[0]
+        q = H['q']
         cross = (D[:-1] >= 0) != (D[1:] >= 0)
         near = cross & (np.minimum(np.abs(D[:-1]), np.abs(D[1:])) < tol)
+        near |= cross & ((np.abs(q[:-1] - 0.5) < q_band) | (np.abs(q[1:] - 0.5) < q_band))
         keep = Z.rows >= Z.js if s == 1 else Z.rows < Z.js
         amb[Z.rows[keep]] |= near.any(axis=0)[keep]
     return amb

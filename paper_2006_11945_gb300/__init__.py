@@ -87,7 +87,7 @@ def load(path: Optional[str] = None):
     lib.egb_get_solve_info.argtypes = [vp, u64, P(egb_solve_info)]
     lib.egb_read_state.argtypes = [vp, u64, vp]
     lib.egb_read_velocity.argtypes = [vp, u64, vp]
-    lib.egb_zmarch.argtypes = [vp, u64, P(d), i, P(d), d, i, d, d, vp, vp, vp, vp, i, P(egb_zmarch_info)]
+    lib.egb_zmarch.argtypes = [vp, u64, P(d), i, P(d), d, i, d, d, i, vp, vp, vp, vp, i, P(egb_zmarch_info)]
     for name in EXPORTED:
         if name != 'egb_last_error':
             getattr(lib, name).restype = i
@@ -173,7 +173,7 @@ def egb_superpose_noalloc(h, solve, u_out=None, count=None, T=None, A=None, kmax
 
 
 def egb_zmarch(h, medium, xs, omegas, beam_width, n_theta, theta_max, cfl=0.5, u_out=None, count=None,
-               T=None, A=None, kmax=8):
+               T=None, A=None, kmax=8, drt=0):
     """The paper's paraxial depth march from the source row, both branches, with its same-row
     superposition (see include/egb.h).  Returns the run's egb_zmarch_info as a dict."""
     om = (ctypes.c_double * max(len(omegas), 1))(*[float(w) for w in omegas])
@@ -181,7 +181,7 @@ def egb_zmarch(h, medium, xs, omegas, beam_width, n_theta, theta_max, cfl=0.5, u
     x = (ctypes.c_double * 3)(*((xs[0], 0.0, xs[1]) if len(xs) == 2 else xs))
     info = egb_zmarch_info()
     _check(h, load().egb_zmarch(h, medium, x, len(omegas), om, float(beam_width), int(n_theta),
-                                 float(theta_max), float(cfl), _ptr(u_out), _ptr(count), _ptr(T),
+                                 float(theta_max), float(cfl), int(drt), _ptr(u_out), _ptr(count), _ptr(T),
                                  _ptr(A), kmax, ctypes.byref(info)))
     out = {k: getattr(info, k) for k, _ in egb_zmarch_info._fields_}
     out['n_sub'], out['rows'] = list(info.n_sub), list(info.rows)
@@ -308,7 +308,7 @@ class Context:
         egb_release(self.h, m)
         return res, info
 
-    def zmarch(self, medium, problem, n_theta, theta_max, cfl=0.5, kmax=8):
+    def zmarch(self, medium, problem, n_theta, theta_max, cfl=0.5, kmax=8, drt=0):
         """Depth march of a 2-D problem's source on `medium` (both branches); returns the outputs
         (u (n_omega, nz, nx), count, T, A) like superpose."""
         nz, nx = problem.nz, problem.nx
@@ -317,7 +317,7 @@ class Context:
         T = np.zeros((nz, nx, kmax), np.float64)
         A = np.zeros((nz, nx, kmax), np.float32)
         egb_zmarch(self.h, medium, problem.xs, problem.omegas, problem.beam_width, n_theta, theta_max,
-                   cfl, u, cnt, T, A, kmax)
+                   cfl, u, cnt, T, A, kmax, drt)
         return SolveResult(u, cnt, T, A)
 
     def solve_problem(self, problem, steps=None, kmax=8):

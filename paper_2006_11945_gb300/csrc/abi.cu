@@ -663,8 +663,9 @@ egb_status egb_superpose_noalloc(egb_ctx *c, egb_solve_id sid, void *u_out, uint
 }
 
 egb_status egb_zmarch(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_omega, const double *omega,
-                      double beam_width, int n_theta, double theta_max, double cfl, void *u_out,
-                      uint8_t *count, double *T, float *A, int kmax, egb_zmarch_info *info) {
+                      double beam_width, int n_theta, double theta_max, double cfl, int drt,
+                      void *u_out, uint8_t *count, double *T, float *A, int kmax,
+                      egb_zmarch_info *info) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->media.find(mid);
@@ -680,6 +681,7 @@ egb_status egb_zmarch(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     if (n_theta < 4 || n_theta > 4096) return fail(c, EGB_E_INVALID, "n_theta must be in 4..4096");
     if (!(theta_max > 0 && theta_max < 0.5 * M_PI)) return fail(c, EGB_E_INVALID, "theta_max must be in (0, pi/2)");
     if (!(cfl > 0 && cfl <= 1.0)) return fail(c, EGB_E_INVALID, "cfl must be in (0, 1]");
+    if (drt != 0 && drt != 1) return fail(c, EGB_E_INVALID, "drt must be 0 or 1");
     bool want_arr = count || T || A;
     if (want_arr && (kmax < 1 || kmax > 32)) return fail(c, EGB_E_INVALID, "kmax must be in 1..32");
     if (m->nx < 4 || m->nz < 2) return fail(c, EGB_E_INVALID, "the depth march needs nx >= 4 and nz >= 2");
@@ -700,6 +702,7 @@ egb_status egb_zmarch(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     P.cfl = cfl;
     P.w0 = beam_width;
     P.n_omega = n_omega;
+    P.drt = drt;
     size_t nodes = (size_t)m->nx * m->nz;
     size_t ub = (size_t)n_omega * nodes * 8;
     size_t need = zmarch_device_bytes(P, m->nx, m->nz) + ub + nodes * (1 + 12 * (size_t)kmax);

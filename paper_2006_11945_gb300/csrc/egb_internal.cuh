@@ -248,6 +248,7 @@ struct ZmParams {
     double cfl;
     double w0;          // beam width (m)
     int n_omega;
+    int drt;            // 0: dynamic ray tracing from label gradients, 1: advected (Eq. 21)
 };
 size_t zmarch_device_bytes(const ZmParams &P, int nx, int nz);
 cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_dev, float2 *u,

@@ -11,18 +11,20 @@
 //  k_zm_coef      per node of the branch's rows, every angle: qP group velocity and phase-angle rate
 //                 (Eqs. 8-12) -> U, W, S and the superposition's Vx, Vz, v, dp_x/dt; the largest CFL
 //                 rate; a latched error where s Vz <= 0 (Eq. 13 violated)
-//  k_zm_init      Eq. 20 on the source row (also its history row)
+//  k_zm_init      Eq. 20 on the source row (also its history row), source indicator q = 1
 //  k_zm_stage<S>  one Shu-Osher stage of one depth substep: third-order HJ-WENO in x and theta,
 //                 differences beyond the ends clamped to the outermost one (identical to ghost cells
 //                 holding the linear extrapolation of the two outermost values), coefficients
-//                 interpolated linearly between the two rows; the last stage of a row records the
-//                 row's labels in the history volume
-//  k_zm_centres   per (row, angle): sign changes of D along x are beam centres; dynamic ray tracing
+//                 interpolated linearly between the two rows; the source indicator q is advected
+//                 with ghost cells holding 0 (rays entering through a boundary carry no source-plane
+//                 data); the last stage of a row records the row's labels in the history volume
+//  k_zm_centres   per (row, angle): sign changes of D along x between cells with q > 1/2 are
+//                 beam centres; dynamic ray tracing
 //                 from the label gradients at fixed depth (the perturbation with db = 1 and the
 //                 initial transverse beam Hessian of Eq. 24) -> M_xx (Eq. 25), spreading and amplitude
 //                 (Eq. 26), weight (Eq. 33), exp(i omega tau) reduced in double-float
 //  k_zm_sum       per receiver: sum over the beams centred on its row (Eq. 34)
-//  k_zm_arrivals  per receiver: sign changes of D along theta -> traveltime and geometrical amplitude
+//  k_zm_arrivals  per receiver: sign changes of D along theta (q > 1/2) -> traveltime and amplitude
 //                 of every arrival (late arrivals included)
 #include <algorithm>
 #include <cmath>
@@ -60,16 +62,24 @@ __device__ __forceinline__ float weno2h(const float d[4], bool left, float eps) 
 struct StageArgs {
     Geom G;
     float ihx, idth, h, t, coef;
-    float eps[3];               // D, vartheta, tau
+    float eps[4];               // D, vartheta, tau, q
     const float *c0, *c1;       // coefficient rows r and r + 1 (U plane; W, S at +cst, +2 cst)
     int64_t cst;                // floats between the U, W and S planes of the table
-    const float *in, *un;       // [4][nth][nx]: D, vartheta, tau_hi, tau_lo
+    const float *in, *un;       // [5][nth][nx]: D, vartheta, tau_hi, tau_lo, q
     float *out;
     float *hist;                // history row to record (D plane of row r + 1), or null
     int64_t hfield, hk;         // history strides: per field, per angle
+    // advected dynamic ray tracing (Eq. 21): Jacobian rows r, r + 1 of (U, W) in (x, theta)
+    // (U_x plane; U_theta, W_x, W_theta at +cst, +2 cst, +3 cst); Q fields are planes 5..8 of the
+    // state and history (dx_1, dtheta_1, dx_2, dtheta_2)
+    const float *j0, *j1;
+    float qeps[4];
 };
 
-template <int STAGE>
+constexpr int NF_LABELS = 5;   // D, vartheta, tau_hi, tau_lo, q
+constexpr int NF_DRT = 9;      // + dx_1, dtheta_1, dx_2, dtheta_2
+
+template <int STAGE, bool QDRT>
 __global__ void __launch_bounds__(128) k_zm_stage(StageArgs A) {
     const int nx = A.G.nx, nth = A.G.nth;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
@@ -111,7 +121,27 @@ __global__ void __launch_bounds__(128) k_zm_stage(StageArgs A) {
         }
         L[2] = S + fmaf(cx, weno2h(dx, lx, A.eps[2]), ct * weno2h(dt, lt, A.eps[2]));
     }
-    float o[4];
+    float Lq;
+    {
+        // source indicator: its ghost cells hold 0 (rays entering through a boundary)
+        const float *F = A.in + 4 * P;
+        auto qv = [&](int kk, int ii) {
+            return (kk < 0 || kk >= nth || ii < 0 || ii >= nx) ? 0.f : F[(int64_t)kk * nx + ii];
+        };
+        float sx[5], st[5], dx[4], dt[4];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            sx[j] = qv(k, i + j - 2);
+            st[j] = qv(k + j - 2, i);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            dx[j] = sx[j + 1] - sx[j];
+            dt[j] = st[j + 1] - st[j];
+        }
+        Lq = fmaf(cx, weno2h(dx, lx, A.eps[3]), ct * weno2h(dt, lt, A.eps[3]));
+    }
+    float o[5];
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
         float u = A.in[f * P + c];
@@ -126,22 +156,95 @@ __global__ void __launch_bounds__(128) k_zm_stage(StageArgs A) {
         o[2] = r.hi;
         o[3] = r.lo;
     }
+    {
+        float u = A.in[4 * P + c];
+        float n = (STAGE == 1) ? u : A.un[4 * P + c];
+        o[4] = fmaf(A.coef, fmaf(A.h, Lq, u - n), n);
+    }
 #pragma unroll
-    for (int f = 0; f < 4; ++f) A.out[f * P + c] = o[f];
+    for (int f = 0; f < 5; ++f) A.out[f * P + c] = o[f];
     if (STAGE == 3 && A.hist) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) A.hist[f * A.hfield + (int64_t)k * A.hk + i] = o[f];
+        for (int f = 0; f < 5; ++f) A.hist[f * A.hfield + (int64_t)k * A.hk + i] = o[f];
+    }
+    if (QDRT) {
+        // Q_zeta + U Q_x + W Q_theta = J Q for the two perturbation families (Eq. 21 in the march's
+        // variables), ghosts by linear extrapolation (clamped differences) like the labels
+        float J[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            J[e] = fmaf(A.t, A.j1[e * A.cst + c] - A.j0[e * A.cst + c], A.j0[e * A.cst + c]);
+        float Lq4[4], qv[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const float *F = A.in + (5 + f) * P;
+            float dx[4], dt[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                dx[j] = F[(int64_t)k * nx + ix[j] + 1] - F[(int64_t)k * nx + ix[j]];
+                dt[j] = F[(int64_t)(it[j] + 1) * nx + i] - F[(int64_t)it[j] * nx + i];
+            }
+            Lq4[f] = fmaf(cx, weno2h(dx, lx, A.qeps[f]), ct * weno2h(dt, lt, A.qeps[f]));
+            qv[f] = F[c];
+        }
+#pragma unroll
+        for (int fam = 0; fam < 2; ++fam) {
+            const float qx = qv[2 * fam], qt = qv[2 * fam + 1];
+            Lq4[2 * fam] += fmaf(J[0], qx, J[1] * qt);
+            Lq4[2 * fam + 1] += fmaf(J[2], qx, J[3] * qt);
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            float u = qv[f];
+            float n = (STAGE == 1) ? u : A.un[(5 + f) * P + c];
+            float ov = fmaf(A.coef, fmaf(A.h, Lq4[f], u - n), n);
+            A.out[(5 + f) * P + c] = ov;
+            if (STAGE == 3 && A.hist) A.hist[(5 + f) * A.hfield + (int64_t)k * A.hk + i] = ov;
+        }
     }
 }
 
-__global__ void k_zm_init(Geom G, const float2 *sc, const double *theta, float *st, float *hist,
-                          int64_t hfield, int64_t hk) {
+// Jacobian of the characteristic field (U, W) in (x, theta) on every cell of the branch's rows:
+// second-order centred differences of the tabulated U, W, one-sided at the ends (as for the labels).
+// Jt: [4][nr][nth][nx] (U_x, U_theta, W_x, W_theta).
+__global__ void k_zm_jac(Geom G, const float *C, float *Jt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y, k = blockIdx.z;
+    if (i >= G.nx) return;
+    const int64_t T = (int64_t)G.nr * G.nth * G.nx;
+    const int nx = G.nx, nth = G.nth;
+    const float ihx = (float)(0.5 / G.hx), idt = 0.5f / G.dth;
+    auto at = [&](int comp, int kk, int ii) { return C[comp * T + ((int64_t)r * nth + kk) * nx + ii]; };
+    auto gx = [&](int comp) {
+        if (i == 0) return (4.f * (at(comp, k, 1) - at(comp, k, 0)) - (at(comp, k, 2) - at(comp, k, 0))) * ihx;
+        if (i == nx - 1) return (4.f * (at(comp, k, nx - 1) - at(comp, k, nx - 2)) - (at(comp, k, nx - 1) - at(comp, k, nx - 3))) * ihx;
+        return (at(comp, k, i + 1) - at(comp, k, i - 1)) * ihx;
+    };
+    auto gt = [&](int comp) {
+        if (k == 0) return (4.f * (at(comp, 1, i) - at(comp, 0, i)) - (at(comp, 2, i) - at(comp, 0, i))) * idt;
+        if (k == nth - 1) return (4.f * (at(comp, nth - 1, i) - at(comp, nth - 2, i)) - (at(comp, nth - 1, i) - at(comp, nth - 3, i))) * idt;
+        return (at(comp, k + 1, i) - at(comp, k - 1, i)) * idt;
+    };
+    const int64_t o = ((int64_t)r * nth + k) * nx + i;
+    Jt[o] = gx(0);
+    Jt[T + o] = gt(0);
+    Jt[2 * T + o] = gx(1);
+    Jt[3 * T + o] = gt(1);
+}
+
+__global__ void k_zm_init(Geom G, const float2 *sc, const double *theta, const float *src, int nf,
+                          float *st, float *hist, int64_t hfield, int64_t hk) {
     int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
     if (i >= G.nx) return;
-    (void)sc;
     int64_t P = (int64_t)G.nth * G.nx, c = (int64_t)k * G.nx + i;
-    float v[4] = {(float)(G.ox + i * G.hx - G.xs), (float)theta[k], 0.f, 0.f};
-    for (int f = 0; f < 4; ++f) {
+    float v[NF_DRT] = {(float)(G.ox + i * G.hx - G.xs), (float)theta[k], 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    if (nf > NF_LABELS) {
+        // offset family Q1 = (1 / ghat_z, 0) of the source medium at theta_k; Q2 = (0, 1)
+        float as[21];
+        for (int q = 0; q < 21; ++q) as[q] = src[q];
+        SrcVel sv = source_velocity(as, sc[k].x, sc[k].y);
+        v[5] = sv.Vn / sv.Vz;
+    }
+    for (int f = 0; f < nf; ++f) {
         st[f * P + c] = v[f];
         hist[f * hfield + (int64_t)k * hk + i] = v[f];
     }
@@ -218,6 +321,7 @@ struct SupArgsZ {
     float w0;
     float C1, C2, C3;
     unsigned *err;
+    int drt;                    // 1: perturbations from the advected Q fields (history planes 5..8)
 };
 
 __device__ __forceinline__ float hval(const SupArgsZ &A, int f, int k, int r, int i) {
@@ -280,6 +384,7 @@ __global__ void k_zm_centres(SupArgsZ A) {
     for (int i = 0; i + 1 < G.nx; ++i) {
         float D0 = hval(A, 0, k, r, i), D1 = hval(A, 0, k, r, i + 1);
         if ((D0 >= 0.f) == (D1 >= 0.f)) continue;
+        if (!(hval(A, 4, k, r, i) > 0.5f && hval(A, 4, k, r, i + 1) > 0.5f)) continue;
         if (cnt >= KC) { atomicOr(A.err, DeviceErrors::OVERFLOW); break; }
         float t = D0 / (D0 - D1);
         auto L = [t](float a, float b) { return a + t * (b - a); };
@@ -305,6 +410,14 @@ __global__ void k_zm_centres(SupArgsZ A) {
         float vth = cth * Vx - sth * Vz;
         float dpx_dth = (cth * v - sth * vth) / (v * v);
         float wj = fabsf(Tt * Dx - Tx * Dt) / fabsf(Dx);
+        float qx1 = 0.f, qt1 = 0.f, qx2 = 0.f, qt2 = 0.f;
+        if (A.drt) {
+            qx1 = L(hval(A, 5, k, r, i), hval(A, 5, k, r, i + 1));
+            qt1 = L(hval(A, 6, k, r, i), hval(A, 6, k, r, i + 1));
+            qx2 = L(hval(A, 7, k, r, i), hval(A, 7, k, r, i + 1));
+            qt2 = L(hval(A, 8, k, r, i), hval(A, 8, k, r, i + 1));
+            wj = 1.f / fabsf(qt2);  // |det J2| / |D_x| in terms of the advected families
+        }
         float wreal = G.dth * wj * c_ref * c_ref / (4.f * 3.14159265358979f * sv.v * sv.v);
         float r0 = 1.f / gsz;
         int64_t slot = slot0 + cnt;
@@ -317,6 +430,10 @@ __global__ void k_zm_centres(SupArgsZ A) {
             // (dx, dtheta) = J2^-1 (r0, i kap), J2 = [[D_x, D_theta], [vartheta_x, vartheta_theta]]
             cfz dx = {Tt * r0 / det, -Dt * kap / det};
             cfz dth = {-Tx * r0 / det, Dx * kap / det};
+            if (A.drt) {  // Q1 + kappa Q2 (Eq. 21 advected)
+                dx = cfz{qx1, kap * qx2};
+                dth = cfz{qt1, kap * qt2};
+            }
             cfz dpx = {pxl * pdx * dx.re + dpx_dth * dth.re, pxl * pdx * dx.im + dpx_dth * dth.im};
             cfz M = zdiv(dpx, dx);
             cfz J = {dx.re * Vz, dx.im * Vz};
@@ -395,12 +512,17 @@ __global__ void k_zm_arrivals(SupArgsZ A, int r_first, uint8_t *count, double *T
         float ss, cs;
         sincosf(thl, &ss, &cs);
         SrcVel sv = source_velocity(as, ss, cs);
+        if (A.drt) {  // point-source family: J_t = |dx_2 Vz|, A = c^2 sqrt(rho_s/rho_r) / (v_s sqrt(8 pi J_t))
+            float Jt = fabsf(hval(A, 7, k, r, i) * A.V[A.vt + o]);
+            return c_ref * c_ref * sqrtf(rho_s / rho_r) / (sv.v * sqrtf(pi8 * Jt));
+        }
         float Dt = grad_t(A, 0, k, r, i, idth);
         return c_ref * c_ref * sqrtf(rho_s / rho_r) / (vr * sqrtf(pi8 * fabsf(sv.Vz) * fabsf(Dt)));
     };
     for (int k = 0; k + 1 < G.nth; ++k) {
         float D0 = hval(A, 0, k, r, i), D1 = hval(A, 0, k + 1, r, i);
         if ((D0 >= 0.f) == (D1 >= 0.f)) continue;
+        if (!(hval(A, 4, k, r, i) > 0.5f && hval(A, 4, k + 1, r, i) > 0.5f)) continue;
         ++total;
         float t = D0 / (D0 - D1);
         float h0 = hval(A, 2, k, r, i), l0 = hval(A, 3, k, r, i);
@@ -470,8 +592,9 @@ size_t zmarch_device_bytes(const ZmParams &P, int nx, int nz) {
     size_t js = (size_t)P.js;
     size_t nr = std::max((size_t)nz - js, js + 1);
     size_t cells = nr * P.n_theta * nx;
-    size_t b = cells * 4 * (3 + 4 + 4);                          // coefficients, velocities, history
-    b += (size_t)3 * 4 * P.n_theta * nx * 4;                      // march buffers
+    const size_t nf = P.drt ? NF_DRT : NF_LABELS;
+    size_t b = cells * 4 * (3 + 4 + nf + (P.drt ? 4 : 0));       // coefficients, velocities, history, J
+    b += (size_t)3 * nf * P.n_theta * nx * 4;                     // march buffers
     b += nr * P.n_theta * (4 + (size_t)KC * (8 + 16 * P.n_omega)); // beam-centre lists
     return b + (1 << 20);
 }
@@ -539,10 +662,12 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         const int64_t plane = (int64_t)nth * nx, T3 = (int64_t)nr * plane;
         float *C = (float *)alloc((size_t)3 * T3 * 4);
         float *V = (float *)alloc((size_t)4 * T3 * 4);
-        float *H = (float *)alloc((size_t)4 * T3 * 4);
-        float *S0 = (float *)alloc((size_t)4 * plane * 4);
-        float *S1 = (float *)alloc((size_t)4 * plane * 4);
-        float *S2 = (float *)alloc((size_t)4 * plane * 4);
+        const int nf = P.drt ? NF_DRT : NF_LABELS;
+        float *H = (float *)alloc((size_t)nf * T3 * 4);
+        float *S0 = (float *)alloc((size_t)nf * plane * 4);
+        float *S1 = (float *)alloc((size_t)nf * plane * 4);
+        float *S2 = (float *)alloc((size_t)nf * plane * 4);
+        float *Jt = P.drt ? (float *)alloc((size_t)4 * T3 * 4) : nullptr;
         int *cnt = (int *)alloc((size_t)nr * nth * 4);
         float *pos = (float *)alloc((size_t)nr * nth * KC * 4);
         float *px = (float *)alloc((size_t)nr * nth * KC * 4);
@@ -552,6 +677,7 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
         if (e != cudaSuccess) break;
         k_zm_coef<<<dim3((nx + 127) / 128, nr), 128, 0, st>>>(m, G, sc, C, V, rate, d_err);
+        if (P.drt) k_zm_jac<<<dim3((nx + 127) / 128, nr, nth), 128, 0, st>>>(G, C, Jt);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         float hrate = 0.f;
         e = cudaMemcpyAsync(&hrate, rate, 4, cudaMemcpyDeviceToHost, st);
@@ -565,12 +691,12 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         stats.rows[bi] = nr;
         stats.cell_updates += (uint64_t)(nr - 1) * n_sub * nth * nx;
         stats.stage_passes += (uint64_t)3 * (nr - 1) * n_sub;
-        stats.kernel_launches += 2 + (uint64_t)3 * (nr - 1) * n_sub;
+        stats.kernel_launches += 2 + (P.drt ? 1 : 0) + (uint64_t)3 * (nr - 1) * n_sub;
         stats.setup_ms += lap(0, 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         const int64_t hk = (int64_t)nr * nx;  // history floats per angle
         dim3 pg((nx + 127) / 128, nth);
-        k_zm_init<<<pg, 128, 0, st>>>(G, sc, theta, S0, H, T3, hk);
+        k_zm_init<<<pg, 128, 0, st>>>(G, sc, theta, src, nf, S0, H, T3, hk);
         StageArgs A;
         A.G = G;
         A.ihx = (float)(1.0 / m.hx);
@@ -580,23 +706,37 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         A.eps[0] = (float)(1e-6 * h * h);
         A.eps[1] = (float)(1e-6 * dth * dth);
         A.eps[2] = (float)(1e-6 * (h / c_ref) * (h / c_ref));
+        A.eps[3] = 1e-6f;
         A.cst = T3;
+        // Q fields' scales: dx_1 ~ 1, dtheta_1 ~ 1/h, dx_2 ~ h per radian, dtheta_2 ~ 1
+        A.qeps[0] = 1e-6f;
+        A.qeps[1] = (float)(1e-6 / (h * h));
+        A.qeps[2] = (float)(1e-6 * h * h);
+        A.qeps[3] = 1e-6f;
+        A.j0 = A.j1 = nullptr;
         float *cur = S0, *oa = S1, *ob = S2;
         for (int r = 0; r + 1 < nr && e == cudaSuccess; ++r) {
             A.c0 = C + (int64_t)r * plane;
             A.c1 = C + (int64_t)(r + 1) * plane;
+            if (P.drt) {
+                A.j0 = Jt + (int64_t)r * plane;
+                A.j1 = Jt + (int64_t)(r + 1) * plane;
+            }
             for (int q = 0; q < n_sub; ++q) {
                 const double t0 = (double)q / n_sub, dt = 1.0 / n_sub;
                 A.hist = nullptr;
                 A.hfield = T3;
                 A.hk = hk;
                 A.in = cur; A.un = cur; A.out = oa; A.coef = 1.f; A.t = (float)t0;
-                k_zm_stage<1><<<pg, 128, 0, st>>>(A);
+                if (P.drt) k_zm_stage<1, true><<<pg, 128, 0, st>>>(A);
+                else k_zm_stage<1, false><<<pg, 128, 0, st>>>(A);
                 A.in = oa; A.un = cur; A.out = ob; A.coef = 0.25f; A.t = (float)(t0 + dt);
-                k_zm_stage<2><<<pg, 128, 0, st>>>(A);
+                if (P.drt) k_zm_stage<2, true><<<pg, 128, 0, st>>>(A);
+                else k_zm_stage<2, false><<<pg, 128, 0, st>>>(A);
                 A.in = ob; A.un = cur; A.out = oa; A.coef = (float)(2.0 / 3.0); A.t = (float)(t0 + 0.5 * dt);
                 if (q + 1 == n_sub) A.hist = H + (int64_t)(r + 1) * nx;
-                k_zm_stage<3><<<pg, 128, 0, st>>>(A);
+                if (P.drt) k_zm_stage<3, true><<<pg, 128, 0, st>>>(A);
+                else k_zm_stage<3, false><<<pg, 128, 0, st>>>(A);
                 std::swap(cur, oa);
             }
             e = cudaGetLastError();
@@ -621,6 +761,7 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         Z.w0 = (float)P.w0;
         Z.C1 = C1; Z.C2 = C2; Z.C3 = C3;
         Z.err = d_err;
+        Z.drt = P.drt;
         const int r_first = s > 0 ? 0 : 1;  // the source row belongs to the downgoing branch
         if (u && P.n_omega > 0) {
             k_zm_centres<<<(nr * nth + 127) / 128, 128, 0, st>>>(Z);

@@ -6,7 +6,8 @@ nodes whose count hinges on a sign of X - x_s below 2e-4 h, traveltimes <= 1e-5 
 <= 1e-3 relative where the counts agree.  Cases: homogeneous VTI, heterogeneous TTI, a focusing lens
 (triplicated arrivals), a ragged grid with the source off the centre column, sources on the top
 row (no upgoing branch), on the bottom row (no march downward) and one row below the top; invalid
-arguments; a medium where a branch's rays turn horizontal.  Full size (the timed workload's
+arguments; a medium where a branch's rays turn horizontal; the dynamic ray tracing advected with
+the march (Eq. 21, drt = 1) against its own oracle.  Full size (the timed workload's
 512 x 512 grid, 256 angles per branch, 5 m): homogeneous VTI against the closed-form traveltimes
 and geometrical amplitudes of straight group rays at every node of the central cone.
 """
@@ -184,3 +185,20 @@ def test_full_size_tti_depth_march_agrees_with_the_pseudo_time_solve():
           np.median(eT), eT.max(), 'A rel median / q99', np.median(eA), np.quantile(eA, 0.99))
     assert np.median(eT) < 2e-4 and eT.max() < 2e-3
     assert np.median(eA) < 1e-2 and np.quantile(eA, 0.99) < 5e-2
+
+
+@pytest.mark.parametrize('name', ['vti48', 'tti64', 'lens64'])
+def test_zmarch_advected_drt_matches_the_oracle(name):
+    """drt = 1: the beams' and arrivals' dynamic ray tracing advected with the march (Eq. 21)
+    against oracle/zmarch_drt.py, at the same bar."""
+    from oracle import zmarch_drt as DR
+    p, nth = _case(name)
+    import paper_2006_11945_gb300 as egb
+    with egb.Context(0) as ctx:
+        res = ctx.zmarch(ctx.medium_2d(p), p, nth, THETA_MAX, 0.5, 8, drt=1)
+    ref = DR.solve(p, nth, THETA_MAX, 0.5)
+    m = _compare(res, ref, p, ref['parts'])
+    print(name, 'drt', m)
+    assert m['u_rel_l2'] < 2e-3, m
+    assert m['count_mismatch'] == 0 and m['arrivals'] > 100, m
+    assert m['T_rel_max'] < 1e-5 and m['A_rel_max'] < 1e-3, m

@@ -12,7 +12,9 @@ Checked against things the march does not compute itself:
   A = sqrt(v / (8 pi r));
 * homogeneous VTI: the far field of the exact plane-wave integral (stationary phase);
 * a low-velocity lens: arrival counts (single and triplicated) and first-arrival traveltimes of the
-  Lagrangian ray shooter.
+  Lagrangian ray shooter;
+* the source indicator against straight rays traced back to the source row (inflow through the
+  x edges).
 """
 import math
 import types
@@ -36,7 +38,7 @@ def _fake(nth, nx, nr, U, W, S, h=1.0, dth=0.05):
     Z.n_sub = 3
     Z.x = h * np.arange(nx)
     Z.theta = dth * (np.arange(nth) - nth / 2 + 0.5)
-    Z.eps = {'X': 1e-6, 'Th': 1e-6, 'tau': 1e-6}
+    Z.eps = {'X': 1e-6, 'Th': 1e-6, 'tau': 1e-6, 'q': 1e-6}
     return Z
 
 
@@ -179,3 +181,21 @@ def test_lens_late_arrivals_match_the_ray_shooter():
     mm = m & (sc >= 1)
     rel = np.abs(res['T'][..., 0][mm] - first[mm]) / first[mm]
     assert np.median(rel) < 1e-3 and rel.max() < 1e-2
+
+
+def test_source_indicator_marks_rays_entering_through_the_edges():
+    """Homogeneous VTI: a cell's straight group ray traced back reaches the source row at
+    x - (z - z_s) Vx/Vz; where that point lies more than 4 cells outside the grid the ray entered
+    through an edge (q < 1/2), more than 4 cells inside it carries source-plane labels (q > 1/2)."""
+    p = synthmedia.vti_homogeneous(n=48, n_theta=32, steps=1)
+    m = p.meta
+    Z = ZM.ZSetup(p, 32, THETA_MAX, 1, 0.5)
+    H = ZM.march(Z)
+    v, Vx, Vz = CF.vti_group_velocity(Z.theta, m['vp0'], m['vs0'], m['eps'], m['delta'])
+    zeta = (Z.rows * p.hz + p.origin[1] - p.xs[1])[None, :, None]
+    x0 = Z.x[None, None, :] - zeta * (Vx / Vz)[:, None, None]
+    lo, hi, h = Z.x[0], Z.x[-1], p.hx
+    outside = (x0 < lo - 4 * h) | (x0 > hi + 4 * h)
+    inside = (x0 > lo + 4 * h) & (x0 < hi - 4 * h)
+    assert outside.sum() > 1000 and inside.sum() > 1000
+    assert np.all(H['q'][outside] < 0.5) and np.all(H['q'][inside] > 0.5)
