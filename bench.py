@@ -459,10 +459,15 @@ def fp64_form(p, steps, device):
             'note': 'plain FP64 stencil, one thread per cell, evolution only'}
 
 
-# Depth march (--workload zmarch): per (theta, x) cell and stage launch the four state fields are
-# read (16 B) and written (16 B), u^n is read in stages 2 and 3 (16 B) and the coefficients U, W, S of
-# the two bounding rows are read (24 B): (56 + 72 + 72) / 3 B per cell and launch.
-ALGO_BYTES_PER_CELL_STAGE_ZM = (56.0 + 72.0 + 72.0) / 3.0
+# Depth march (--workload zmarch): per (theta, x) cell and stage launch the nf state fields are
+# read and written (4 nf B each), u^n is read in stages 2 and 3 (4 nf B) and the coefficients U, W, S
+# of the two bounding rows are read (24 B); with the advected dynamic ray tracing (nf = 9 instead of
+# 5) also the Jacobian of (U, W) of the two rows (32 B).  Averaged over the three stage launches.
+def algo_bytes_per_cell_stage_zm(drt):
+    nf = 9 if drt else 5
+    rows = 24 + (32 if drt else 0)
+    s1 = 8 * nf + rows
+    return (s1 + 2 * (s1 + 4 * nf)) / 3.0
 
 
 def run_zmarch(args):
@@ -494,7 +499,8 @@ def run_zmarch(args):
         c21, rho = (c21_h, rho_h) if host else (c21_d, rho_d)
         m = egb.egb_medium(ctx.h, (p.nx, 1, p.nz), (p.hx, 1.0, p.hz), (p.origin[0], 0.0, p.origin[1]), c21, rho)
         u, cnt, T, A = outs_h if host else outs_d
-        info = egb.egb_zmarch(ctx.h, m, p.xs, p.omegas, p.beam_width, nth, tmax, p.cfl, u, cnt, T, A, kmax)
+        info = egb.egb_zmarch(ctx.h, m, p.xs, p.omegas, p.beam_width, nth, tmax, p.cfl, u, cnt, T, A, kmax,
+                              drt=args.zm_drt)
         egb.egb_release(ctx.h, m)
         infos.append(info)
         return info
@@ -522,7 +528,7 @@ def run_zmarch(args):
     e2e_ms, _ = timed(True, max(1, args.steps), 1)
     cu = info['cell_updates']
     launch_ms = march_ms / info['stage_passes']
-    achieved = ALGO_BYTES_PER_CELL_STAGE_ZM * nth * p.nx / (launch_ms / 1e3) / 1e9
+    achieved = algo_bytes_per_cell_stage_zm(args.zm_drt) * nth * p.nx / (launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     h2d = p.c21.nbytes + p.rho.nbytes
     d2h = sum(o.numel() * o.element_size() for o in outs_h)
@@ -533,7 +539,9 @@ def run_zmarch(args):
         'dtype': 'f32 (double-float tau and phase)', 'data': 'synthetic (seeded TTI medium)',
         'config': {'workload': f'paraxial depth march (Eqs. 13-20), {p.name} {p.nx}x{p.nz} at {p.hx:g} m, '
                                f'{nth} angles per branch within +-{args.zm_theta_max:g} deg, both branches, '
-                               f'{len(p.freqs)} frequencies', 'cells_per_row': nth * p.nx,
+                               f'{len(p.freqs)} frequencies, dynamic ray tracing '
+                               f'{"advected (Eq. 21)" if args.zm_drt else "from label gradients"}',
+                   'cells_per_row': nth * p.nx, 'drt': args.zm_drt,
                    'n_sub': info['n_sub'], 'rows': info['rows'], 'freqs_hz': p.freqs,
                    'l2': 'per-row state (2 MB) L2-resident; coefficient and history volumes (1.9 GB) larger than L2, no flush'},
         'solves_per_s': args.steps / (ms / 1e3),
@@ -722,6 +730,7 @@ def main():
                              'zmarch'])
     ap.add_argument('--zm-theta', type=int, default=256)
     ap.add_argument('--zm-n', type=int, default=512)
+    ap.add_argument('--zm-drt', type=int, default=0, choices=[0, 1])
     ap.add_argument('--zm-theta-max', type=float, default=60.0)
     ap.add_argument('--batch-count', type=int, default=6)
     ap.add_argument('--serve-seconds', type=float, default=2.0)
