@@ -233,14 +233,14 @@ egb_status egb_read_velocity(egb_ctx *ctx, egb_solve_id solve, float *out);
  * Rays entering through the grid's x edges or the ends of the angle range carry no source-plane
  * labels: an advected source indicator (ghost value 0) keeps them out of beams and arrivals.
  * Synchronous: returns when the outputs are written.  The work buffers (about 48 bytes per
- * phase-space cell of the larger branch) are allocated and freed by the call; EGB_E_NOMEM when
- * they do not fit. */
+ * phase-space cell of both branches together, which advance in the same launches) are allocated
+ * and freed by the call; EGB_E_NOMEM when they do not fit. */
 typedef struct {
     int n_sub[2];             /* TVD-RK3 substeps per row interval: [0] downgoing, [1] upgoing (0: absent) */
     int rows[2];              /* rows of each branch, the source row included */
     uint64_t cell_updates;    /* (theta, x) cells advanced one full substep, both branches */
-    uint64_t stage_passes;    /* stage kernel launches, each one pass over the (theta, x) plane
-                               * (3 per substep) */
+    uint64_t stage_passes;    /* stage passes over a branch's (theta, x) plane (3 per substep and
+                               * branch); branches with equal substep counts share launches */
     uint64_t kernel_launches; /* every kernel the call launched */
     double setup_ms;          /* device time of the characteristic tables (CUDA events, ctx stream) */
     double march_ms;          /* device time of the depth march (initial data and stages) */

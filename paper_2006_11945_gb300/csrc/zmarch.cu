@@ -80,10 +80,8 @@ constexpr int NF_LABELS = 5;   // D, vartheta, tau_hi, tau_lo, q
 constexpr int NF_DRT = 9;      // + dx_1, dtheta_1, dx_2, dtheta_2
 
 template <int STAGE, bool QDRT>
-__global__ void __launch_bounds__(128) k_zm_stage(StageArgs A) {
+__device__ __forceinline__ void stage_body(const StageArgs &A, int k, int i) {
     const int nx = A.G.nx, nth = A.G.nth;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
-    if (i >= nx) return;
     const int64_t P = (int64_t)nth * nx;
     const int64_t c = (int64_t)k * nx + i;
     const float U = fmaf(A.t, A.c1[c] - A.c0[c], A.c0[c]);
@@ -202,6 +200,17 @@ __global__ void __launch_bounds__(128) k_zm_stage(StageArgs A) {
             if (STAGE == 3 && A.hist) A.hist[(5 + f) * A.hfield + (int64_t)k * A.hk + i] = ov;
         }
     }
+}
+
+// One stage over the (theta, x) planes of one or two branches (blockIdx.z selects the branch): the
+// two branches are independent until the superposition, so advancing both in one launch doubles the
+// cells a launch covers.
+template <int STAGE, bool QDRT>
+__global__ void __launch_bounds__(128) k_zm_stage(const __grid_constant__ StageArgs A0,
+                                                  const __grid_constant__ StageArgs A1) {
+    const StageArgs &A = blockIdx.z ? A1 : A0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (i < A.G.nx && k < A.G.nth) stage_body<STAGE, QDRT>(A, k, i);
 }
 
 // Jacobian of the characteristic field (U, W) in (x, theta) on every cell of the branch's rows:
@@ -589,12 +598,12 @@ static void split_2pi(float &C1, float &C2, float &C3) {
 }
 
 size_t zmarch_device_bytes(const ZmParams &P, int nx, int nz) {
-    size_t js = (size_t)P.js;
-    size_t nr = std::max((size_t)nz - js, js + 1);
+    // both branches are resident at once: nz - js rows downward and js + 1 upward
+    size_t nr = (size_t)nz + 1;
     size_t cells = nr * P.n_theta * nx;
     const size_t nf = P.drt ? NF_DRT : NF_LABELS;
     size_t b = cells * 4 * (3 + 4 + nf + (P.drt ? 4 : 0));       // coefficients, velocities, history, J
-    b += (size_t)3 * nf * P.n_theta * nx * 4;                     // march buffers
+    b += (size_t)2 * 3 * nf * P.n_theta * nx * 4;                 // march buffers of both branches
     b += nr * P.n_theta * (4 + (size_t)KC * (8 + 16 * P.n_omega)); // beam-centre lists
     return b + (1 << 20);
 }
@@ -618,8 +627,6 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         return (double)ms;
     };
     float *src = nullptr, *rate = nullptr;
-    float2 *sc = nullptr;
-    double *theta = nullptr;
     std::vector<void *> bufs;
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
@@ -629,8 +636,6 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
     };
     src = (float *)alloc(32 * 4);
     rate = (float *)alloc(4);
-    sc = (float2 *)alloc((size_t)nth * 8);
-    theta = (double *)alloc((size_t)nth * 8);
     float c_ref = 0.f;  // source phase velocity along +z (scales the tau WENO epsilon)
     if (e == cudaSuccess) {
         zm::k_zm_source<<<1, 32, 0, st>>>(m, P.xs, P.zs, src);
@@ -641,44 +646,59 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
     }
     float C1, C2, C3;
     split_2pi(C1, C2, C3);
-    for (int s : {1, -1}) {
-        if (e != cudaSuccess) break;
-        const int nr = s > 0 ? nz - P.js : P.js + 1;
-        if (s < 0 && nr < 2) break;  // no row above the source
-        // phase angles of the branch (double on the host, then sin / cos rounded to float)
+    // Phase 1, per branch: phase angles, characteristic tables, substep count, initial data.
+    struct Branch {
+        bool on = false;
+        int s = 1, nr = 0, n_sub = 0, nf = NF_LABELS;
+        Geom G;
+        int64_t plane = 0, T3 = 0;
+        float2 *sc = nullptr;
+        double *theta = nullptr;
+        float *C = nullptr, *V = nullptr, *H = nullptr, *Jt = nullptr, *S[3] = {nullptr, nullptr, nullptr};
+        int *cnt = nullptr;
+        float *pos = nullptr, *px = nullptr;
+        float4 *dat = nullptr;
+        StageArgs A;
+        float *cur = nullptr, *oa = nullptr, *ob = nullptr;
+    } br[2];
+    const double dth = 2.0 * P.theta_max / nth;
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        Branch &B = br[b];
+        B.s = b == 0 ? 1 : -1;
+        B.nr = B.s > 0 ? nz - P.js : P.js + 1;
+        if (B.s < 0 && B.nr < 2) continue;  // no row above the source
+        B.on = true;
+        B.nf = P.drt ? NF_DRT : NF_LABELS;
         std::vector<double> th(nth);
         std::vector<float2> schost(nth);
-        const double dth = 2.0 * P.theta_max / nth;
-        for (int k = 0; k < nth; ++k) {
-            th[k] = -P.theta_max + (k + 0.5) * dth + (s > 0 ? 0.0 : M_PI);
+        for (int k = 0; k < nth; ++k) {  // double on the host, then sin / cos rounded to float
+            th[k] = -P.theta_max + (k + 0.5) * dth + (B.s > 0 ? 0.0 : M_PI);
             schost[k] = make_float2((float)sin(th[k]), (float)cos(th[k]));
         }
-        e = cudaMemcpyAsync(theta, th.data(), (size_t)nth * 8, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sc, schost.data(), (size_t)nth * 8, cudaMemcpyHostToDevice, st);
-        Geom G;
-        G.nx = nx; G.nth = nth; G.nr = nr; G.js = P.js; G.s = s;
+        B.sc = (float2 *)alloc((size_t)nth * 8);
+        B.theta = (double *)alloc((size_t)nth * 8);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.theta, th.data(), (size_t)nth * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.sc, schost.data(), (size_t)nth * 8, cudaMemcpyHostToDevice, st);
+        Geom &G = B.G;
+        G.nx = nx; G.nth = nth; G.nr = B.nr; G.js = P.js; G.s = B.s;
         G.hx = m.hx; G.hz = m.hz; G.ox = m.ox; G.xs = P.xs;
         G.dth = (float)dth;
-        const int64_t plane = (int64_t)nth * nx, T3 = (int64_t)nr * plane;
-        float *C = (float *)alloc((size_t)3 * T3 * 4);
-        float *V = (float *)alloc((size_t)4 * T3 * 4);
-        const int nf = P.drt ? NF_DRT : NF_LABELS;
-        float *H = (float *)alloc((size_t)nf * T3 * 4);
-        float *S0 = (float *)alloc((size_t)nf * plane * 4);
-        float *S1 = (float *)alloc((size_t)nf * plane * 4);
-        float *S2 = (float *)alloc((size_t)nf * plane * 4);
-        float *Jt = P.drt ? (float *)alloc((size_t)4 * T3 * 4) : nullptr;
-        int *cnt = (int *)alloc((size_t)nr * nth * 4);
-        float *pos = (float *)alloc((size_t)nr * nth * KC * 4);
-        float *px = (float *)alloc((size_t)nr * nth * KC * 4);
-        float4 *dat = (float4 *)alloc((size_t)P.n_omega * nr * nth * KC * 16 + 16);
+        B.plane = (int64_t)nth * nx;
+        B.T3 = (int64_t)B.nr * B.plane;
+        B.C = (float *)alloc((size_t)3 * B.T3 * 4);
+        B.V = (float *)alloc((size_t)4 * B.T3 * 4);
+        B.H = (float *)alloc((size_t)B.nf * B.T3 * 4);
+        for (auto &x : B.S) x = (float *)alloc((size_t)B.nf * B.plane * 4);
+        B.Jt = P.drt ? (float *)alloc((size_t)4 * B.T3 * 4) : nullptr;
+        B.cnt = (int *)alloc((size_t)B.nr * nth * 4);
+        B.pos = (float *)alloc((size_t)B.nr * nth * KC * 4);
+        B.px = (float *)alloc((size_t)B.nr * nth * KC * 4);
+        B.dat = (float4 *)alloc((size_t)P.n_omega * B.nr * nth * KC * 16 + 16);
+        if (e == cudaSuccess) e = cudaMemsetAsync(rate, 0, 4, st);
         if (e != cudaSuccess) break;
-        e = cudaMemsetAsync(rate, 0, 4, st);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        if (e != cudaSuccess) break;
-        k_zm_coef<<<dim3((nx + 127) / 128, nr), 128, 0, st>>>(m, G, sc, C, V, rate, d_err);
-        if (P.drt) k_zm_jac<<<dim3((nx + 127) / 128, nr, nth), 128, 0, st>>>(G, C, Jt);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        k_zm_coef<<<dim3((nx + 127) / 128, B.nr), 128, 0, st>>>(m, G, B.sc, B.C, B.V, rate, d_err);
+        if (P.drt) k_zm_jac<<<dim3((nx + 127) / 128, B.nr, nth), 128, 0, st>>>(G, B.C, B.Jt);
         float hrate = 0.f;
         e = cudaMemcpyAsync(&hrate, rate, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -686,18 +706,15 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         int n_sub = (int)std::ceil(m.hz * (double)hrate / P.cfl);
         if (!(n_sub >= 1)) n_sub = 1;
         if (n_sub > 4096) n_sub = 4096;  // a branch flagged invalid still terminates
-        const int bi = s > 0 ? 0 : 1;
-        stats.n_sub[bi] = n_sub;
-        stats.rows[bi] = nr;
-        stats.cell_updates += (uint64_t)(nr - 1) * n_sub * nth * nx;
-        stats.stage_passes += (uint64_t)3 * (nr - 1) * n_sub;
-        stats.kernel_launches += 2 + (P.drt ? 1 : 0) + (uint64_t)3 * (nr - 1) * n_sub;
-        stats.setup_ms += lap(0, 1);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        const int64_t hk = (int64_t)nr * nx;  // history floats per angle
-        dim3 pg((nx + 127) / 128, nth);
-        k_zm_init<<<pg, 128, 0, st>>>(G, sc, theta, src, nf, S0, H, T3, hk);
-        StageArgs A;
+        B.n_sub = n_sub;
+        stats.n_sub[b] = n_sub;
+        stats.rows[b] = B.nr;
+        stats.cell_updates += (uint64_t)(B.nr - 1) * n_sub * nth * nx;
+        stats.stage_passes += (uint64_t)3 * (B.nr - 1) * n_sub;
+        stats.kernel_launches += 2 + (P.drt ? 1 : 0);
+        const int64_t hk = (int64_t)B.nr * nx;  // history floats per angle
+        k_zm_init<<<dim3((nx + 127) / 128, nth), 128, 0, st>>>(G, B.sc, B.theta, src, B.nf, B.S[0], B.H, B.T3, hk);
+        StageArgs &A = B.A;
         A.G = G;
         A.ihx = (float)(1.0 / m.hx);
         A.idth = (float)(1.0 / dth);
@@ -707,62 +724,110 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
         A.eps[1] = (float)(1e-6 * dth * dth);
         A.eps[2] = (float)(1e-6 * (h / c_ref) * (h / c_ref));
         A.eps[3] = 1e-6f;
-        A.cst = T3;
+        A.cst = B.T3;
         // Q fields' scales: dx_1 ~ 1, dtheta_1 ~ 1/h, dx_2 ~ h per radian, dtheta_2 ~ 1
         A.qeps[0] = 1e-6f;
         A.qeps[1] = (float)(1e-6 / (h * h));
         A.qeps[2] = (float)(1e-6 * h * h);
         A.qeps[3] = 1e-6f;
         A.j0 = A.j1 = nullptr;
-        float *cur = S0, *oa = S1, *ob = S2;
-        for (int r = 0; r + 1 < nr && e == cudaSuccess; ++r) {
-            A.c0 = C + (int64_t)r * plane;
-            A.c1 = C + (int64_t)(r + 1) * plane;
+        A.hfield = B.T3;
+        A.hk = hk;
+        B.cur = B.S[0]; B.oa = B.S[1]; B.ob = B.S[2];
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    // Phase 2: the march.  Row interval r of every branch that has one; branches with the same
+    // substep count advance together, one launch per stage for both.
+    const int rmax = std::max(br[0].on ? br[0].nr - 1 : 0, br[1].on ? br[1].nr - 1 : 0);
+    const bool fuse = br[0].on && br[1].on && br[0].n_sub == br[1].n_sub;
+    auto launch = [&](int stage, Branch *b0, Branch *b1) {
+        dim3 g((nx + 127) / 128, nth, b1 ? 2 : 1);
+        const StageArgs &a0 = b0->A, &a1 = b1 ? b1->A : b0->A;
+        if (P.drt) {
+            if (stage == 1) k_zm_stage<1, true><<<g, 128, 0, st>>>(a0, a1);
+            else if (stage == 2) k_zm_stage<2, true><<<g, 128, 0, st>>>(a0, a1);
+            else k_zm_stage<3, true><<<g, 128, 0, st>>>(a0, a1);
+        } else {
+            if (stage == 1) k_zm_stage<1, false><<<g, 128, 0, st>>>(a0, a1);
+            else if (stage == 2) k_zm_stage<2, false><<<g, 128, 0, st>>>(a0, a1);
+            else k_zm_stage<3, false><<<g, 128, 0, st>>>(a0, a1);
+        }
+        stats.kernel_launches += 1;
+    };
+    // one substep q of row interval r for the branches in list (1 or 2 of them)
+    auto substep = [&](Branch **list, int n, int r, int q) {
+        for (int j = 0; j < n; ++j) {
+            Branch &B = *list[j];
+            const double t0 = (double)q / B.n_sub;
+            B.A.c0 = B.C + (int64_t)r * B.plane;
+            B.A.c1 = B.C + (int64_t)(r + 1) * B.plane;
             if (P.drt) {
-                A.j0 = Jt + (int64_t)r * plane;
-                A.j1 = Jt + (int64_t)(r + 1) * plane;
+                B.A.j0 = B.Jt + (int64_t)r * B.plane;
+                B.A.j1 = B.Jt + (int64_t)(r + 1) * B.plane;
             }
-            for (int q = 0; q < n_sub; ++q) {
-                const double t0 = (double)q / n_sub, dt = 1.0 / n_sub;
-                A.hist = nullptr;
-                A.hfield = T3;
-                A.hk = hk;
-                A.in = cur; A.un = cur; A.out = oa; A.coef = 1.f; A.t = (float)t0;
-                if (P.drt) k_zm_stage<1, true><<<pg, 128, 0, st>>>(A);
-                else k_zm_stage<1, false><<<pg, 128, 0, st>>>(A);
-                A.in = oa; A.un = cur; A.out = ob; A.coef = 0.25f; A.t = (float)(t0 + dt);
-                if (P.drt) k_zm_stage<2, true><<<pg, 128, 0, st>>>(A);
-                else k_zm_stage<2, false><<<pg, 128, 0, st>>>(A);
-                A.in = ob; A.un = cur; A.out = oa; A.coef = (float)(2.0 / 3.0); A.t = (float)(t0 + 0.5 * dt);
-                if (q + 1 == n_sub) A.hist = H + (int64_t)(r + 1) * nx;
-                if (P.drt) k_zm_stage<3, true><<<pg, 128, 0, st>>>(A);
-                else k_zm_stage<3, false><<<pg, 128, 0, st>>>(A);
-                std::swap(cur, oa);
-            }
+            B.A.hist = nullptr;
+            B.A.in = B.cur; B.A.un = B.cur; B.A.out = B.oa; B.A.coef = 1.f; B.A.t = (float)t0;
+        }
+        launch(1, list[0], n > 1 ? list[1] : nullptr);
+        for (int j = 0; j < n; ++j) {
+            Branch &B = *list[j];
+            const double t0 = (double)q / B.n_sub, dt = 1.0 / B.n_sub;
+            B.A.in = B.oa; B.A.un = B.cur; B.A.out = B.ob; B.A.coef = 0.25f; B.A.t = (float)(t0 + dt);
+        }
+        launch(2, list[0], n > 1 ? list[1] : nullptr);
+        for (int j = 0; j < n; ++j) {
+            Branch &B = *list[j];
+            const double t0 = (double)q / B.n_sub, dt = 1.0 / B.n_sub;
+            B.A.in = B.ob; B.A.un = B.cur; B.A.out = B.oa; B.A.coef = (float)(2.0 / 3.0);
+            B.A.t = (float)(t0 + 0.5 * dt);
+            if (q + 1 == B.n_sub) B.A.hist = B.H + (int64_t)(r + 1) * nx;
+        }
+        launch(3, list[0], n > 1 ? list[1] : nullptr);
+        for (int j = 0; j < n; ++j) std::swap(list[j]->cur, list[j]->oa);
+    };
+    if (fuse) {
+        for (int r = 0; r < rmax && e == cudaSuccess; ++r) {
+            Branch *list[2];
+            int n = 0;
+            for (auto &B : br)
+                if (r + 1 < B.nr) list[n++] = &B;
+            for (int q = 0; q < br[0].n_sub; ++q) substep(list, n, r, q);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-        if (e != cudaSuccess) break;
+    } else {
+        for (auto &B : br) {
+            if (!B.on) continue;
+            Branch *list[1] = {&B};
+            for (int r = 0; r + 1 < B.nr && e == cudaSuccess; ++r) {
+                for (int q = 0; q < B.n_sub; ++q) substep(list, 1, r, q);
+                e = cudaGetLastError();
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+    // Phase 3, per branch: beams and arrivals on the rows it owns.
+    for (auto &B : br) {
+        if (!B.on || e != cudaSuccess) continue;
         SupArgsZ Z;
-        Z.G = G;
-        Z.H = H;
-        Z.hf = T3;
-        Z.V = V;
-        Z.vt = T3;
+        Z.G = B.G;
+        Z.H = B.H;
+        Z.hf = B.T3;
+        Z.V = B.V;
+        Z.vt = B.T3;
         Z.rho = m.rho;
         Z.src = src;
-        Z.sc = sc;
-        Z.cnt = cnt;
-        Z.pos = pos;
-        Z.px = px;
-        Z.dat = dat;
+        Z.sc = B.sc;
+        Z.cnt = B.cnt;
+        Z.pos = B.pos;
+        Z.px = B.px;
+        Z.dat = B.dat;
         Z.n_omega = P.n_omega;
         Z.omega = omega_dev;
         Z.w0 = (float)P.w0;
         Z.C1 = C1; Z.C2 = C2; Z.C3 = C3;
         Z.err = d_err;
         Z.drt = P.drt;
-        const int r_first = s > 0 ? 0 : 1;  // the source row belongs to the downgoing branch
+        const int nr = B.nr, r_first = B.s > 0 ? 0 : 1;  // the source row belongs to the downgoing branch
         if (u && P.n_omega > 0) {
             k_zm_centres<<<(nr * nth + 127) / 128, 128, 0, st>>>(Z);
             k_zm_sum<<<dim3((nx + 127) / 128, nr - r_first), 128, 0, st>>>(Z, r_first, u, nz);
@@ -773,14 +838,12 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
             stats.kernel_launches += 1;
         }
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        stats.march_ms += lap(1, 2);
-        stats.superpose_ms += lap(2, 3);
-        // this branch's buffers are done: free them before the next branch
-        for (size_t q = 4; q < bufs.size(); ++q) cudaFree(bufs[q]);
-        bufs.resize(4);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    stats.setup_ms = lap(0, 1);
+    stats.march_ms = lap(1, 2);
+    stats.superpose_ms = lap(2, 3);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (void *p : bufs) cudaFree(p);
     for (auto &x : ev)
