@@ -7,15 +7,12 @@ import pytest
 
 import synthmedia
 from oracle import liouville as L
-from oracle import shooter as SH
 from oracle import superpose as SP
 
 
 @pytest.fixture(scope='module')
-def both():
-    p = synthmedia.tti_heterogeneous(n=64, n_theta=64, length=2560.0, steps=400, freqs=(10.0,))
-    fan = SH.shoot(p, n_rays=2048)
-    cnt, first, arr = SH.arrivals(p, fan)
+def both(tti64_shooter):
+    p, fan, cnt, first, arr = tti64_shooter
     S, st, dt = L.evolve(p)
     lab = L.interior_state(st, S)
     ec, eT, eA, _ = SP.arrivals(S, lab, 8)

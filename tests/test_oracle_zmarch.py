@@ -167,9 +167,9 @@ def lens_problem(n=64, h=10.0):
 
 def test_lens_late_arrivals_match_the_ray_shooter():
     p = lens_problem()
-    fan = SH.shoot(p, n_rays=4096)
+    fan = SH.shoot(p, n_rays=2048)
     sc, first, _ = SH.arrivals(p, fan)
-    res = ZM.solve(p, 128, THETA_MAX, 0.5)
+    res = ZM.solve(p, 96, THETA_MAX, 0.5)
     x = np.arange(p.nx) * p.hx - p.xs[0]
     z = np.arange(p.nz) * p.hz - p.xs[1]
     Zg, Xg = np.meshgrid(z, x, indexing='ij')

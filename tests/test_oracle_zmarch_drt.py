@@ -14,7 +14,6 @@ import pytest
 
 import synthmedia
 from oracle import closed_forms as CF
-from oracle import shooter as SH
 from oracle import zmarch as ZM
 from oracle import zmarch_drt as DR
 
@@ -66,10 +65,8 @@ def test_homogeneous_isotropic_wavefield():
 
 
 @pytest.fixture(scope='module')
-def tti():
-    p = synthmedia.tti_heterogeneous(n=64, n_theta=64, length=2560.0, steps=400, freqs=(10.0,))
-    fan = SH.shoot(p, n_rays=2048)
-    sc, first, arr = SH.arrivals(p, fan)
+def tti(tti64_shooter):
+    p, fan, sc, first, arr = tti64_shooter
     return p, sc, arr, ZM.solve(p, 64, THETA_MAX, 0.5), DR.solve(p, 64, THETA_MAX, 0.5)
 
 
