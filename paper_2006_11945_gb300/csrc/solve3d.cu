@@ -387,17 +387,18 @@ struct Stage3Args {
 
 // Work decomposition: blockIdx.x = direction cell (fastest, so that the CTAs resident at a time
 // cover many directions of one spatial tile and the theta/phi neighbours of a cell are read from L2),
-// blockIdx.y = 64 x 4 tile in (x, y), blockIdx.z = chunk of ZC3 z slices marched by the CTA (the z
+// blockIdx.y = 64 x TY3 tile in (x, y), blockIdx.z = chunk of ZC3 z slices marched by the CTA (the z
 // neighbours of the next slice are the ones just read).
 constexpr int ZC3 = 8;
+constexpr int TY3 = 8;    // y rows of a tile (256 threads, 64 registers: 4 blocks per SM)
 
 template <int STAGE>
-__global__ void __launch_bounds__(128, 8) k_rk3_3d(Stage3Args A) {
+__global__ void __launch_bounds__(32 * TY3, 32 / TY3) k_rk3_3d(Stage3Args A) {
     const Grid3D &g = A.g;
     int nxt = (g.nx + 63) / 64;
     int dir = blockIdx.x;
     int ix = 2 * ((blockIdx.y % nxt) * 32 + threadIdx.x);
-    int iy = (blockIdx.y / nxt) * 4 + threadIdx.y;
+    int iy = (blockIdx.y / nxt) * TY3 + threadIdx.y;
     if (ix >= g.nx || iy >= g.ny) return;
     int zend = min((int)(blockIdx.z + 1) * ZC3, g.nz);
     for (int iz = blockIdx.z * ZC3; iz < zend; ++iz) {
@@ -509,8 +510,8 @@ cudaError_t solve3d_evolve(Solve3D &sv, int steps, cudaStream_t s) {
     A.eps[1] = 1e-6f;
     A.eps[2] = 1e-6f;
     A.eps[3] = (float)(1e-6 * (h / sv.c_ref) * (h / sv.c_ref));
-    dim3 block(32, 4);
-    dim3 grid(g.nph * g.nth, ((g.nx + 63) / 64) * ((g.ny + 3) / 4), (g.nz + ZC3 - 1) / ZC3);
+    dim3 block(32, TY3);
+    dim3 grid(g.nph * g.nth, ((g.nx + 63) / 64) * ((g.ny + TY3 - 1) / TY3), (g.nz + ZC3 - 1) / ZC3);
     float *U = sv.state[0], *B = sv.state[1], *C = sv.state[2];
     for (int st = 0; st < steps; ++st) {
         A.un = U;
