@@ -127,13 +127,16 @@ def test_zmarch_rejects_invalid_arguments_and_turning_rays():
         assert status(call) == egb.EGB_OK        # the context stays usable
 
 
-def test_zmarch_full_size_homogeneous_vti_against_straight_rays():
+@pytest.mark.parametrize('drt', [0, 1])
+def test_zmarch_full_size_homogeneous_vti_against_straight_rays(drt):
     """The timed workload's grid and angle sampling (512 x 512 at 5 m, 256 angles per branch,
     theta_max 60 deg, source at the centre) in a homogeneous VTI medium: one arrival per node of
     the cone |group angle| < 45 deg beyond 20 m, with T = r / |V_g| and A = |u_GO| sqrt(omega) of
-    the closed-form far field."""
+    the closed-form far field, for both dynamic ray tracing routes."""
+    import paper_2006_11945_gb300 as egb
     p = synthmedia.vti_homogeneous(n=512, h=5.0, n_theta=256, steps=1, freqs=(20.0,))
-    res = _gpu(p, 256)
+    with egb.Context(0) as ctx:
+        res = ctx.zmarch(ctx.medium_2d(p), p, 256, THETA_MAX, 0.5, 8, drt=drt)
     m_ = p.meta
     x = np.arange(p.nx) * p.hx - p.xs[0]
     z = np.arange(p.nz) * p.hz - p.xs[1]
@@ -170,6 +173,7 @@ def test_full_size_tti_depth_march_agrees_with_the_pseudo_time_solve():
         pt, _ = ctx.solve_problem(p)
         m = ctx.medium_2d(p)
         zm = ctx.zmarch(m, p, 256, THETA_MAX)
+        zq = ctx.zmarch(m, p, 256, THETA_MAX, drt=1)
     x = np.arange(p.nx) * p.hx - p.xs[0]
     z = np.arange(p.nz) * p.hz - p.xs[1]
     Zg, Xg = np.meshgrid(z, x, indexing='ij')
@@ -185,6 +189,11 @@ def test_full_size_tti_depth_march_agrees_with_the_pseudo_time_solve():
           np.median(eT), eT.max(), 'A rel median / q99', np.median(eA), np.quantile(eA, 0.99))
     assert np.median(eT) < 2e-4 and eT.max() < 2e-3
     assert np.median(eA) < 1e-2 and np.quantile(eA, 0.99) < 5e-2
+    # the advected point-source family's amplitudes (drt = 1) agree as well
+    bq = both & (zq.count == 1)
+    eQ = np.abs(zq.A[..., 0][bq] - pt.A[..., 0][bq]) / pt.A[..., 0][bq]
+    print('advected DRT amplitudes vs pseudo-time: median', np.median(eQ), 'q99', np.quantile(eQ, 0.99))
+    assert np.median(eQ) < 1e-2 and np.quantile(eQ, 0.99) < 5e-2
 
 
 @pytest.mark.parametrize('name', ['vti48', 'tti64', 'lens64'])
