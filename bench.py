@@ -142,6 +142,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, dist, device):
+    """The largest per-rank time of a timed region (every rank receives it); ms on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ranks, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time (weak
+    scaling: every rank runs its own replica of the workload)."""
+    return ranks * units_per_rank / (ms / 1e3)
+
+
 def run_egb(args):
     import torch
     import paper_2006_11945_gb300 as egb
@@ -212,11 +228,7 @@ def run_egb(args):
         with torch.cuda.stream(stream):
             t1.record(stream)
         torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1)
-        if dist is not None:
-            t = torch.tensor([ms], device='cuda')
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(t0.elapsed_time(t1), dist, 'cuda')
         return ms, info
 
     with ClockSampler(local) as clk:
@@ -226,8 +238,8 @@ def run_egb(args):
     cells = info['cells']
     cu_per_solve = cells * steps_evolve
     per_step_ms = ms / args.steps
-    value = ws * cu_per_solve * args.steps / (ms / 1e3)
-    e2e_value = ws * cu_per_solve * max(1, args.steps) / (e2e_ms / 1e3)
+    value = job_rate(cu_per_solve * args.steps, ws, ms)
+    e2e_value = job_rate(cu_per_solve * max(1, args.steps), ws, e2e_ms)
     peak, peak_kind = measured_peaks()
     launch_ms = evolve_avg_ms / (3 * steps_evolve)
     achieved = ALGO_BYTES_PER_CELL_UPDATE * cells / 3.0 / (launch_ms / 1e3) / 1e9
