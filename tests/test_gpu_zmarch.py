@@ -211,3 +211,39 @@ def test_zmarch_advected_drt_matches_the_oracle(name):
     assert m['u_rel_l2'] < 2e-3, m
     assert m['count_mismatch'] == 0 and m['arrivals'] > 100, m
     assert m['T_rel_max'] < 1e-5 and m['A_rel_max'] < 1e-3, m
+
+
+def test_zmarch_output_pointers_and_arrival_capacity():
+    """Device outputs equal host outputs bit for bit; an arrivals-only call (no frequencies, no
+    wavefield) gives the same arrivals; with capacity 1 the lens's triplicated nodes report
+    EGB_E_ARRIVAL_OVERFLOW and keep their earliest arrival."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    p = lens_problem()
+    nz, nx = p.nz, p.nx
+    with egb.Context(0) as ctx:
+        m = ctx.medium_2d(p)
+        host = ctx.zmarch(m, p, 96, THETA_MAX)
+        u = torch.zeros((1, nz, nx, 2), dtype=torch.float32, device='cuda')
+        cnt = torch.zeros((nz, nx), dtype=torch.uint8, device='cuda')
+        T = torch.zeros((nz, nx, 8), dtype=torch.float64, device='cuda')
+        A = torch.zeros((nz, nx, 8), dtype=torch.float32, device='cuda')
+        egb.egb_zmarch(ctx.h, m, p.xs, p.omegas, p.beam_width, 96, THETA_MAX, 0.5, u, cnt, T, A, 8)
+        assert np.array_equal(u.cpu().numpy().view(np.complex64)[..., 0], host.u)
+        assert np.array_equal(cnt.cpu().numpy(), host.count)
+        assert np.array_equal(T.cpu().numpy(), host.T) and np.array_equal(A.cpu().numpy(), host.A)
+        c2 = np.zeros((nz, nx), np.uint8)
+        T2 = np.zeros((nz, nx, 8))
+        egb.egb_zmarch(ctx.h, m, p.xs, [], p.beam_width, 96, THETA_MAX, 0.5, None, c2, T2, None, 8)
+        assert np.array_equal(c2, host.count) and np.array_equal(T2, host.T)
+        c1 = np.zeros((nz, nx), np.uint8)
+        T1 = np.zeros((nz, nx, 1))
+        A1 = np.zeros((nz, nx, 1), np.float32)
+        try:
+            egb.egb_zmarch(ctx.h, m, p.xs, [], p.beam_width, 96, THETA_MAX, 0.5, None, c1, T1, A1, 1)
+            status = egb.EGB_OK
+        except egb.EgbError as e:
+            status = e.status
+    assert host.count.max() == 3 and status == egb.EGB_E_ARRIVAL_OVERFLOW
+    assert np.array_equal(c1, np.minimum(host.count, 1))
+    assert np.array_equal(T1[..., 0], host.T[..., 0]) and np.array_equal(A1[..., 0], host.A[..., 0])
