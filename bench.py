@@ -13,6 +13,9 @@ region).  The state (1.3 GB per copy) is far larger than L2, so no flush is need
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl egb|reference]
 Under torchrun every rank runs its own replica (independent solves, no collective): weak scaling.
+Other workloads (--workload): tti256 / tti128 / vti64 (smaller 2-D cases), tri96 / tri48 (3-D),
+batch (uneven batched solves), serve (continuous batching on a Poisson request stream) and zmarch
+(the paper's paraxial depth march, --zm-drt 1 for the dynamic ray tracing advected as Eq. 21).
 """
 from __future__ import annotations
 
