@@ -88,11 +88,13 @@ def test_heterogeneous_wavefield_tends_to_the_shooters_geometrical_field(field12
         om = 2 * math.pi * f
         u = SP.green(S, lab, [om], 150.0)[0][m]
         go = A[m] / math.sqrt(om) * np.exp(1j * (om * T[m] + math.pi / 4))
-        e = np.abs(u - go) / np.abs(go)
-        err[f] = np.median(e)
+        ratio = np.abs(u) / np.abs(go)
+        err[f] = np.median(np.abs(ratio - 1))
         if f == 80.0:
-            assert err[f] < 0.09 and np.quantile(e, 0.9) < 0.2, (err[f], np.quantile(e, 0.9))
-            ratio = np.abs(u) / np.abs(go)
+            # the phase error (omega times the 40 m grid's traveltime error) grows with omega, so the
+            # complex error is bounded here rather than required to fall
+            e = np.abs(u - go) / np.abs(go)
+            assert np.median(e) < 0.09 and np.quantile(e, 0.9) < 0.2, (np.median(e), np.quantile(e, 0.9))
             up, down = np.median(ratio[Z[m] < 0]), np.median(ratio[Z[m] > 0])
             assert abs(up - 1) < 0.03 and abs(down - 1) < 0.03 and abs(up - down) < 0.025, (up, down)
-    assert err[20.0] > err[40.0] > err[80.0], err
+    assert err[20.0] > 2 * err[40.0] and err[40.0] > 1.3 * err[80.0] and err[80.0] < 0.04, err
