@@ -113,6 +113,10 @@ def shoot(problem, n_rays=2048, dt=None, t_max=None):
 def arrivals(problem, fan, min_dist=0.0, node_mask=None):
     """Ray-tube arrivals at the grid nodes: count, sorted times and GO amplitudes per node.
 
+    Each arrival is (T, A, J_t, m), m its KMAH index: the number of caustics the tube has passed,
+    counted as sign changes of the signed spreading dx/dtheta_0 x V along the tube; the arrival's
+    geometrical field is A exp(i (omega T + pi/4 - m pi/2)) / sqrt(omega).
+
     node_mask (nz, nx) bool, optional: collect arrivals only at these nodes (the others report 0),
     which bounds the work on large grids; the arrivals of a node do not depend on the others."""
     X, Z, T = fan['X'], fan['Z'], fan['T']
@@ -132,7 +136,13 @@ def arrivals(problem, fan, min_dist=0.0, node_mask=None):
     # spreading of each tube: |dx/dtheta0 x V| with V ~ (x(t+dt) - x(t)) / dt
     gx, gz = (bx - ax) / dth, (bz - az) / dth
     vx, vz = (dx_ - ax) / (T[1] - T[0]), (dz_ - az) / (T[1] - T[0])
-    Jt = np.abs(gx * vz - gz * vx)
+    Js = gx * vz - gz * vx
+    Jt = np.abs(Js)
+    # KMAH index of each tube: the signed spreading changes sign once per caustic the tube passes
+    sg = np.sign(Js)
+    flips = np.zeros(Js.shape, np.int64)
+    flips[1:] = (sg[1:] * sg[:-1]) < 0
+    kmah = np.cumsum(flips, axis=0)
     out = {}
     s_rho = float(_md.bilinear_at(M.rho, problem, *problem.xs))
     vs = fan['vs']
@@ -140,6 +150,7 @@ def arrivals(problem, fan, min_dist=0.0, node_mask=None):
         Ax, Az, Bx, Bz, Cx, Cz, ta, tb, tc = (np.asarray(q).ravel() for q in tri)
         ray = np.tile(np.arange(nr), ns - 1)
         jt = Jt.ravel()
+        km = kmah.ravel()
         xmin = np.floor((np.minimum(np.minimum(Ax, Bx), Cx) - ox) / problem.hx).astype(int)
         xmax = np.floor((np.maximum(np.maximum(Ax, Bx), Cx) - ox) / problem.hx).astype(int)
         zmin = np.floor((np.minimum(np.minimum(Az, Bz), Cz) - oz) / problem.hz).astype(int)
@@ -170,7 +181,7 @@ def arrivals(problem, fan, min_dist=0.0, node_mask=None):
                     rho_r = float(M.sample(M.rho[..., None], np.array([px[q]]), np.array([pz[q]]))[0, 0])
                     c_ref = float(_ch.source_quantities(fan['a_s'], np.array([0.0]))[0][0])
                     A = c_ref ** 2 * math.sqrt(s_rho / rho_r) / (vs[r] * math.sqrt(8 * math.pi * max(jt[q], 1e-300)))
-                    out.setdefault(key, []).append((tt, A, jt[q]))
+                    out.setdefault(key, []).append((tt, A, jt[q], int(km[q])))
     count = np.zeros((nz, nx), np.int32)
     first = np.full((nz, nx), np.nan)
     arr = {}

@@ -14,7 +14,9 @@ Checked against things the march does not compute itself:
 * a low-velocity lens: arrival counts (single and triplicated) and first-arrival traveltimes of the
   Lagrangian ray shooter;
 * the source indicator against straight rays traced back to the source row (inflow through the
-  x edges).
+  x edges);
+* behind a wide lens, the triplicated wavefield against the shooter's geometrical field with the
+  KMAH phase shift of the arrival that has passed a caustic.
 """
 import math
 import types
@@ -199,3 +201,59 @@ def test_source_indicator_marks_rays_entering_through_the_edges():
     inside = (x0 > lo + 4 * h) & (x0 < hi - 4 * h)
     assert outside.sum() > 1000 and inside.sum() > 1000
     assert np.all(H['q'][outside] < 0.5) and np.all(H['q'][inside] > 0.5)
+
+
+def wide_lens_problem():
+    """Isotropic 128 x 128 medium at 10 m with a 30 % slow Gaussian lens (sigma 120 m) 320 m below
+    the source: behind it a cusp caustic opens a triplication zone several wavelengths wide at
+    200 Hz, whose late arrival has passed one caustic."""
+    n, h = 128, 10.0
+    x = np.arange(n) * h
+    Z, X = np.meshgrid(x, x, indexing='ij')
+    vp = 3000.0 * (1.0 - 0.3 * np.exp(-((X - 640.0) ** 2 + (Z - 420.0) ** 2) / (2 * 120.0 ** 2)))
+    vs, rho = vp / 1.8, 2300.0
+    mu = rho * vs ** 2
+    C = synthmedia.isotropic_voigt(rho * vp ** 2 - 2 * mu, mu)
+    c21 = synthmedia.voigt_to_c21(C).reshape(-1, 21).astype(np.float32)
+    return synthmedia.Problem2D('wide-lens', n, n, h, h, c21, np.full(n * n, rho, np.float32),
+                                (640.0, 100.0), 64, [15.0], 40.0, 200)
+
+
+@pytest.mark.slow
+def test_triplicated_wavefield_carries_the_kmah_phase_shift():
+    """Behind the wide lens, at triplicated nodes at least three cells from any change of the arrival
+    count, the beam sum (Eqs. 25-28 with the amplitude's square root continued through the caustic)
+    tends with frequency to the geometrical field sum_k A_k exp(i (omega T_k + pi/4 - m_k pi/2)) /
+    sqrt(omega) of the Lagrangian shooter, m_k its KMAH index; without the -m_k pi/2 shift the two
+    differ at order one."""
+    from scipy import ndimage
+    p = wide_lens_problem()
+    x = np.arange(p.nx) * p.hx
+    Z, X = np.meshgrid(x, x, indexing='ij')
+    box = (Z >= 700.0) & (np.abs(X - 640.0) <= 250.0)
+    fan = SH.shoot(p, n_rays=2048, dt=1.5e-3)
+    sc, first, arr = SH.arrivals(p, fan, node_mask=box)
+    calm = ndimage.maximum_filter(sc, 7) == ndimage.minimum_filter(sc, 7)
+    m = box & (sc == 3) & calm
+    assert m.sum() >= 30
+    assert all([a[3] for a in arr[key]] == [0, 0, 1] for key in zip(*np.nonzero(m)))
+    freqs = (50.0, 100.0, 200.0)
+    res = ZM.solve(p, 128, THETA_MAX, 0.5, omegas=[2 * math.pi * f for f in freqs], beam_width=40.0)
+    assert np.array_equal(res['count'][box & calm], sc[box & calm])
+    err = {}
+    for w, f in enumerate(freqs):
+        om = 2 * math.pi * f
+        go = np.zeros(sc.shape, complex)
+        go0 = np.zeros(sc.shape, complex)
+        for key in zip(*np.nonzero(m)):
+            for T, A, _, mk in arr[key]:
+                g = A / math.sqrt(om) * np.exp(1j * (om * T + math.pi / 4))
+                go[key] += g * (-1j) ** mk
+                go0[key] += g
+        u = res['u'][w][m]
+        e = np.abs(u - go[m]) / np.abs(go[m])
+        err[f] = np.median(e)
+        if f == 200.0:
+            assert err[f] < 0.06 and np.quantile(e, 0.9) < 0.1, (err[f], np.quantile(e, 0.9))
+            assert np.median(np.abs(u - go0[m]) / np.abs(go0[m])) > 0.5
+    assert err[50.0] > err[100.0] > 2 * err[200.0], err
