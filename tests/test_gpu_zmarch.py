@@ -4,7 +4,8 @@ Eqs. 25-28, 33-35) with the FP64 oracle, through the C ABI.
 Bar (as for the pseudo-time path): wavefield relative L2 <= 2e-3, arrival counts exact outside the
 nodes whose count hinges on a sign of X - x_s below 2e-4 h, traveltimes <= 1e-5 and amplitudes
 <= 1e-3 relative where the counts agree.  Cases: homogeneous VTI, heterogeneous TTI, a focusing lens
-(triplicated arrivals), a ragged grid with the source off the centre column, sources on the top
+(triplicated arrivals) and a wide lens at 100 and 200 Hz (a triplication zone past a caustic), a
+ragged grid with the source off the centre column, sources on the top
 row (no upgoing branch), on the bottom row (no march downward) and one row below the top; invalid
 arguments; a medium where a branch's rays turn horizontal; the dynamic ray tracing advected with
 the march (Eq. 21, drt = 1) against its own oracle.  Full size (the timed workload's
@@ -20,7 +21,7 @@ import pytest
 import synthmedia
 from oracle import closed_forms as CF
 from oracle import zmarch as ZM
-from tests.test_oracle_zmarch import lens_problem
+from tests.test_oracle_zmarch import lens_problem, wide_lens_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -83,6 +84,25 @@ def test_zmarch_matches_the_oracle(name):
     assert m['T_rel_max'] < 1e-5 and m['A_rel_max'] < 1e-3, m
     if name == 'lens64':
         assert res.count.max() == 3
+
+
+def test_zmarch_matches_the_oracle_behind_a_wide_lens_at_high_frequency():
+    """The wide lens at 100 and 200 Hz (beam width 40 m, 128 angles): the triplication zone whose
+    late arrival has passed a caustic, where the oracle's wavefield is pinned against the
+    KMAH-shifted geometrical field; phases omega tau reach about 500 rad."""
+    p = dataclasses.replace(wide_lens_problem(), freqs=[100.0, 200.0])
+    res = _gpu(p, 128)
+    ref = ZM.solve(p, 128, THETA_MAX, 0.5)
+    m = _compare(res, ref, p, ref['parts'])
+    print('wide lens', m)
+    assert m['u_rel_l2'] < 2e-3, m
+    assert m['count_mismatch'] == 0 and m['arrivals'] > 1000, m
+    assert m['T_rel_max'] < 1e-5 and m['A_rel_max'] < 1e-3, m
+    assert np.sum(res.count == 3) > 300
+    for w in range(2):
+        tri = ref['count'] == 3
+        d = np.linalg.norm(res.u[w][tri] - ref['u'][w][tri]) / np.linalg.norm(ref['u'][w][tri])
+        assert d < 2e-3, (w, d)
 
 
 @pytest.mark.parametrize('row', [0, 1, 47])
