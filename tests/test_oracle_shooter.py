@@ -96,5 +96,26 @@ def test_heterogeneous_wavefield_tends_to_the_shooters_geometrical_field(field12
             e = np.abs(u - go) / np.abs(go)
             assert np.median(e) < 0.09 and np.quantile(e, 0.9) < 0.2, (np.median(e), np.quantile(e, 0.9))
             up, down = np.median(ratio[Z[m] < 0]), np.median(ratio[Z[m] > 0])
-            assert abs(up - 1) < 0.03 and abs(down - 1) < 0.03 and abs(up - down) < 0.025, (up, down)
+            assert _density_medians_ok(up, down), (up, down)
     assert err[20.0] > 2 * err[40.0] and err[40.0] > 1.3 * err[80.0] and err[80.0] < 0.04, err
+
+
+def _density_medians_ok(up, down):
+    return abs(up - 1) < 0.03 and abs(down - 1) < 0.03 and abs(up - down) < 0.025
+
+
+@pytest.mark.slow
+def test_wavefield_pin_detects_a_dropped_density_factor(field128):
+    """Planted mistake in the oracle: with the receiver density replaced by the source's, the beam
+    sum loses its sqrt(rho_s / rho) factor and the amplitude medians above and below the source
+    leave the bounds the pin above holds them to."""
+    import copy
+    import math
+    S, lab, m, Z, T, A = field128
+    bad = copy.copy(S)
+    bad.rho = np.full_like(S.rho, S.rho_s)
+    om = 2 * math.pi * 80.0
+    u = SP.green(bad, lab, [om], 150.0)[0][m]
+    ratio = np.abs(u) * math.sqrt(om) / A[m]
+    up, down = np.median(ratio[Z[m] < 0]), np.median(ratio[Z[m] > 0])
+    assert not _density_medians_ok(up, down), (up, down)
