@@ -204,10 +204,15 @@ __device__ __forceinline__ void stage_body(const StageArgs &A, int k, int i) {
 
 // One stage over the (theta, x) planes of one or two branches (blockIdx.z selects the branch): the
 // two branches are independent until the superposition, so advancing both in one launch doubles the
-// cells a launch covers.
+// cells a launch covers.  Stages are launched as programmatic dependents of the one before: every
+// CTA first lets the next stage's grid begin launching (it can start only once all CTAs of this one
+// are running, so it never takes their slots), then waits until the previous grid has completed and
+// its writes are visible, before any load or store.
 template <int STAGE, bool QDRT>
 __global__ void __launch_bounds__(128) k_zm_stage(const __grid_constant__ StageArgs A0,
                                                   const __grid_constant__ StageArgs A1) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const StageArgs &A = blockIdx.z ? A1 : A0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
     if (i < A.G.nx && k < A.G.nth) stage_body<STAGE, QDRT>(A, k, i);
@@ -740,18 +745,30 @@ cudaError_t zmarch_run(const Medium &m, const ZmParams &P, const double *omega_d
     // substep count advance together, one launch per stage for both.
     const int rmax = std::max(br[0].on ? br[0].nr - 1 : 0, br[1].on ? br[1].nr - 1 : 0);
     const bool fuse = br[0].on && br[1].on && br[0].n_sub == br[1].n_sub;
+    // stage launches overlap the previous stage's last wave (programmatic dependent launch)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
     auto launch = [&](int stage, Branch *b0, Branch *b1) {
-        dim3 g((nx + 127) / 128, nth, b1 ? 2 : 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((nx + 127) / 128, nth, b1 ? 2 : 1);
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cfg.attrs = pdl;
+        cfg.numAttrs = 1;
         const StageArgs &a0 = b0->A, &a1 = b1 ? b1->A : b0->A;
+        cudaError_t le;
         if (P.drt) {
-            if (stage == 1) k_zm_stage<1, true><<<g, 128, 0, st>>>(a0, a1);
-            else if (stage == 2) k_zm_stage<2, true><<<g, 128, 0, st>>>(a0, a1);
-            else k_zm_stage<3, true><<<g, 128, 0, st>>>(a0, a1);
+            if (stage == 1) le = cudaLaunchKernelEx(&cfg, k_zm_stage<1, true>, a0, a1);
+            else if (stage == 2) le = cudaLaunchKernelEx(&cfg, k_zm_stage<2, true>, a0, a1);
+            else le = cudaLaunchKernelEx(&cfg, k_zm_stage<3, true>, a0, a1);
         } else {
-            if (stage == 1) k_zm_stage<1, false><<<g, 128, 0, st>>>(a0, a1);
-            else if (stage == 2) k_zm_stage<2, false><<<g, 128, 0, st>>>(a0, a1);
-            else k_zm_stage<3, false><<<g, 128, 0, st>>>(a0, a1);
+            if (stage == 1) le = cudaLaunchKernelEx(&cfg, k_zm_stage<1, false>, a0, a1);
+            else if (stage == 2) le = cudaLaunchKernelEx(&cfg, k_zm_stage<2, false>, a0, a1);
+            else le = cudaLaunchKernelEx(&cfg, k_zm_stage<3, false>, a0, a1);
         }
+        if (le != cudaSuccess && e == cudaSuccess) e = le;
         stats.kernel_launches += 1;
     };
     // one substep q of row interval r for the branches in list (1 or 2 of them)
