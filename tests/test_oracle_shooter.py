@@ -73,6 +73,14 @@ def field128(tti64_shooter):
     return S, lab, m, Z, T, A
 
 
+def test_no_tube_passes_a_caustic_in_the_tti_medium(tti64_shooter):
+    """The medium has no caustic (one arrival at every node reached): the shooter's KMAH counter
+    (sign changes of the signed tube spreading) stays 0 on every arrival."""
+    p, fan, cnt, first, arr = tti64_shooter
+    assert cnt.max() == 1
+    assert all(a[3] == 0 for lst in arr.values() for a in lst)
+
+
 @pytest.mark.slow
 def test_heterogeneous_wavefield_tends_to_the_shooters_geometrical_field(field128):
     """Away from caustics the beam sum (Eq. 34) tends, as omega grows at fixed beam width, to the
