@@ -160,7 +160,11 @@ egb_status egb_superpose(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t 
  *     9 bytes per phase-space cell plus the beam-centre lists, i.e. up to a few million cells) is
  *     refused with EGB_E_INVALID and a message giving both sizes;
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress with
- *     that device current); make that first call before any stream capture;
+ *     that device current); make that first call before any stream capture.  The array is taken
+ *     when the library's superposition module is first loaded on the device; under the runtime's
+ *     default lazy module loading that can be this first call itself (or the first egb_superpose);
+ *   - a solve made in an EGB_FP64 context is superposed from the FP32 rounding of its state,
+ *     written into the solve's own buffers, exactly as egb_superpose does;
  *   - every call shares the array: calls whose kernels may overlap on the GPU (other streams or
  *     other contexts on the same device) race and must be serialised by the caller.
  * It calls no cudaMalloc, cudaFree or other allocating routine. */

@@ -235,8 +235,12 @@ def arrivals(S, lab, kmax=8):
     F = beam_fields(S, lab)
     v_r = S.vel['v']
     rho_r = S.rho[None, :, :]
-    Acell = S.c_ref ** 2 * np.sqrt(S.rho_s / rho_r) / (
-        v_r * np.sqrt(8 * np.pi * F['Vsn'] * np.abs(F['bt'])))
+    # Cells with d b / d theta = 0 (b constant along theta: rays from the boundary, or a caustic of
+    # the point-source family) have no finite geometrical amplitude; they are inf here and must not
+    # reach a counted crossing (checked below).
+    with np.errstate(divide='ignore'):
+        Acell = S.c_ref ** 2 * np.sqrt(S.rho_s / rho_r) / (
+            v_r * np.sqrt(8 * np.pi * F['Vsn'] * np.abs(F['bt'])))
     b, tau, flag = F['b'], F['tau'], F['flag']
     bn, taun, flagn, An = (np.roll(a, -1, axis=0) for a in (b, tau, flag, Acell))
     cross = flag & flagn & ((b >= 0) != (bn >= 0))
@@ -248,7 +252,13 @@ def arrivals(S, lab, kmax=8):
     ks, izs, ixs = np.nonzero(cross)
     t = b[ks, izs, ixs] / (b[ks, izs, ixs] - bn[ks, izs, ixs])
     Tval = tau[ks, izs, ixs] + t * (taun[ks, izs, ixs] - tau[ks, izs, ixs])
-    Aval = Acell[ks, izs, ixs] + t * (An[ks, izs, ixs] - Acell[ks, izs, ixs])
+    with np.errstate(invalid='ignore'):
+        Aval = Acell[ks, izs, ixs] + t * (An[ks, izs, ixs] - Acell[ks, izs, ixs])
+    if not np.all(np.isfinite(Aval)):
+        bad = np.flatnonzero(~np.isfinite(Aval))[0]
+        raise FloatingPointError(
+            'arrival at node (%d, %d), angle cell %d lies on a cell with d b / d theta = 0: '
+            'its geometrical amplitude is undefined' % (izs[bad], ixs[bad], ks[bad]))
     order = np.lexsort((ks, Tval, ixs, izs))
     per_node = {}
     for j in order:

@@ -635,6 +635,7 @@ egb_status egb_superpose_noalloc(egb_ctx *c, egb_solve_id sid, void *u_out, uint
                                  double *T, float *A, int kmax) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
+    if (c->solves3d.count(sid)) return fail(c, EGB_E_INVALID, "3-D solves are not accepted by egb_superpose_noalloc");
     auto it = c->solves.find(sid);
     if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
     if ((count || T || A) && (kmax < 1 || kmax > 32)) return fail(c, EGB_E_INVALID, "kmax must be in 1..32");
@@ -655,7 +656,9 @@ egb_status egb_superpose_noalloc(egb_ctx *c, egb_solve_id sid, void *u_out, uint
     size_t own_bytes = s->scratch_bytes;
     s->scratch = (float *)fixed;
     s->scratch_bytes = EGB_NOALLOC_SCRATCH_BYTES;
-    e = launch_superpose(*s, (float2 *)u_out, count, T, A, kmax, c->d_err, c->stream);
+    // an FP64 solve is superposed from its FP32 rounding, written into the solve's own state[0]
+    if (s->fp64) e = fp64_to_fp32_state(*s, c->stream);
+    if (e == cudaSuccess) e = launch_superpose(*s, (float2 *)u_out, count, T, A, kmax, c->d_err, c->stream);
     s->scratch = own;
     s->scratch_bytes = own_bytes;
     if (e != cudaSuccess) return cuda_fail(c, e, "superpose (fixed scratch)");

@@ -444,7 +444,8 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
 
 // ---------------------------------------------------------------------------------------------
 // Fixed scratch for egb_superpose_noalloc.  Every GPU that loads the library reserves this array
-// when the module is loaded and keeps it until the process exits.  Host code must not pass the
+// when this module is loaded on it (under lazy module loading: at the first launch from this file
+// or the first address lookup below) and keeps it until the process exits.  Host code must not pass the
 // symbol itself to a kernel (in host code it names a host-side stand-in); it asks the runtime for
 // the device address once per device, with that device current, and passes that address.
 // No part of it has to start at zero: each superposition kernel writes every byte it later reads.

@@ -22,19 +22,24 @@ def _outputs(torch, p, kmax):
             torch.zeros((p.nz, p.nx, kmax), dtype=torch.float32, device=dev))
 
 
-def test_noalloc_matches_superpose_on_two_calls():
+@pytest.mark.parametrize('precision', ['fp32_phase64', 'fp64'])
+def test_noalloc_matches_superpose_on_two_calls(precision):
+    """Two calls in a row, the solve evolved further before the second: a call that superposed a
+    stale state (the initial labels, or the previous call's) would differ from egb_superpose."""
     torch = pytest.importorskip('torch')
     import paper_2006_11945_gb300 as egb
     kmax = 8
+    prec = egb.EGB_FP64 if precision == 'fp64' else egb.EGB_FP32_PHASE64
     p = synthmedia.tti_heterogeneous(n=64, n_theta=48, length=2560.0, steps=120, freqs=(10.0, 20.0))
-    with egb.Context(0) as ctx:
+    with egb.Context(0, precision=prec) as ctx:
         m = ctx.medium_2d(p)
         s = ctx.source_2d(m, p)
-        ctx.evolve(s, p.steps, p.cfl)
-        ref = _outputs(torch, p, kmax)
-        egb.egb_superpose(ctx.h, s, *ref, kmax=kmax)
-        egb.egb_sync(ctx.h)
-        for call in range(2):
+        prev = None
+        for call, steps in enumerate((60, 60)):
+            ctx.evolve(s, steps, p.cfl)
+            ref = _outputs(torch, p, kmax)
+            egb.egb_superpose(ctx.h, s, *ref, kmax=kmax)
+            egb.egb_sync(ctx.h)
             out = _outputs(torch, p, kmax)
             egb.egb_superpose_noalloc(ctx.h, s, *out, kmax=kmax)
             egb.egb_sync(ctx.h)
@@ -42,6 +47,10 @@ def test_noalloc_matches_superpose_on_two_calls():
             u = out[0].cpu().numpy().view(np.complex64)[..., 0]
             rel = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)
             assert rel < 2e-3, (call, rel)
+            if prev is not None:
+                # the evolution moved the wavefield, so matching above is not matching a stale copy
+                assert np.linalg.norm(u - prev) / np.linalg.norm(u) > 1e-3, call
+            prev = u
             cnt_ref, cnt = ref[1].cpu().numpy(), out[1].cpu().numpy()
             assert np.array_equal(cnt, cnt_ref), call
             sel = np.arange(kmax)[None, None, :] < cnt_ref[..., None]
@@ -51,7 +60,7 @@ def test_noalloc_matches_superpose_on_two_calls():
             assert np.max(np.abs(A - A_ref) / A_ref) < 1e-3, call
 
 
-def test_noalloc_refuses_oversized_solves_and_host_buffers():
+def test_noalloc_refuses_oversized_solves_3d_ids_and_host_buffers():
     torch = pytest.importorskip('torch')
     import paper_2006_11945_gb300 as egb
     big = synthmedia.vti_homogeneous(n=256, n_theta=128, steps=1)
@@ -69,3 +78,10 @@ def test_noalloc_refuses_oversized_solves_and_host_buffers():
         with pytest.raises(egb.EgbError) as e:
             egb.egb_superpose_noalloc(ctx.h, s2, host_u)
         assert e.value.status == egb.EGB_E_INVALID
+        q = synthmedia.vti_homogeneous_3d(n=8, n_theta=4, n_phi=8, steps=1)
+        m3 = ctx.medium_3d(q)
+        s3 = ctx.source_3d(m3, q)
+        u3 = torch.zeros((1, q.nz, q.ny, q.nx, 2), dtype=torch.float32, device='cuda')
+        with pytest.raises(egb.EgbError) as e:
+            egb.egb_superpose_noalloc(ctx.h, s3, u3)
+        assert e.value.status == egb.EGB_E_INVALID and '3-D' in str(e.value)
