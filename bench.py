@@ -237,19 +237,21 @@ def run_egb(args):
     with ClockSampler(local) as clk:
         ms, info = timed(False, args.steps, args.warmup)
     evolve_avg_ms = float(np.mean(evolve_ms))
-    e2e_ms, _ = timed(True, max(1, args.steps), 1)
+    k_e2e = max(1, min(3, args.steps))
+    e2e_ms, _ = timed(True, k_e2e, 1)
     cells = info['cells']
     cu_per_solve = cells * steps_evolve
     per_step_ms = ms / args.steps
     value = job_rate(cu_per_solve * args.steps, ws, ms)
-    e2e_value = job_rate(cu_per_solve * max(1, args.steps), ws, e2e_ms)
+    e2e_value = job_rate(cu_per_solve * k_e2e, ws, e2e_ms)
     peak, peak_kind = measured_peaks()
     launch_ms = evolve_avg_ms / (3 * steps_evolve)
     achieved = ALGO_BYTES_PER_CELL_UPDATE * cells / 3.0 / (launch_ms / 1e3) / 1e9
     # per timed solve: k_medium_a, k_medium_grad; k_source, k_velocity, k_frozen, k_init,
-    # k_zero_frozen; 3 stage launches per step; k_beam_fields, 2 x k_centres, k_sum, k_arrivals
-    # (the theta-chunk autotuner ran in the warm-up solve and is cached per grid shape)
-    launches = 2 + 5 + 3 * steps_evolve + 5
+    # k_zero_frozen, the first k_track_branch; 3 stage launches per step and a k_track_branch every
+    # 9 steps; k_beam_fields, 2 x k_centres, k_sum, k_arrivals (the theta-chunk autotuner ran in
+    # the warm-up solve and is cached per grid shape)
+    launches = 2 + 6 + 3 * steps_evolve + steps_evolve // 9 + 5
     h2d = p.c21.nbytes + p.rho.nbytes
     d2h = u_h.numel() * 4 + cnt_h.numel() + T_h.numel() * 8 + A_h.numel() * 4
     line = {
@@ -273,7 +275,7 @@ def run_egb(args):
         'solves_per_s': ws * args.steps / (ms / 1e3),
         'beam_point_sums_per_s': ws * args.steps * p.nx * p.nz * p.n_theta * len(p.freqs) / (ms / 1e3),
         'e2e': {'value': e2e_value, 'unit': 'cell-updates/s', 'h2d_bytes_per_step': int(h2d),
-                'd2h_bytes_per_step': int(d2h)},
+                'd2h_bytes_per_step': int(d2h), 'timed_steps': k_e2e},
         'roofline': {'bound': 'hbm', 'kernel': 'k_rk3_tma', 'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': achieved / peak, 'traffic': stencil_traffic_per_launch(cells),
                      'peak_kind': peak_kind, 'launch_ms': launch_ms},
@@ -285,9 +287,20 @@ def run_egb(args):
         line['fp64_form']['speedup'] = line['value'] / ws / line['fp64_form']['value']
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line['cpu_baseline'] = cpu_baseline(p, budget_s=args.cpu_seconds)
+    ctx.close()
+    if ws == 1 and args.workload == 'tti512' and not args.no_sub:
+        # the other configurations of the metric, each measured on its own with its own clocks
+        p3 = workload('tri96')
+        line['sub'] = {
+            'tri96': measure_3d(p3, p3.steps, 1, 1, warmup_steps=3),
+            'batch': measure_batch_waves(synthmedia.batched_instances(count=args.batch_count),
+                                         args.evolve_steps or 10, 1, 1),
+            'serve': measure_serve(args.serve_seconds, 1.0, args.serve_chunk,
+                                   args.serve_wall if args.serve_wall is not None else 60.0,
+                                   args.serve_chunk_work, args.serve_max_chunk_work),
+        }
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -296,10 +309,16 @@ def run_egb3d(args):
     """The 3-D (5-D phase space) workload: whole solves (medium, source, evolve, superpose) through
     the C ABI with --evolve-steps TVD-RK3 steps each (default 20 of the workload's full count)."""
     import torch
-    import paper_2006_11945_gb300 as egb
     torch.cuda.set_device(0)
     p = workload(args.workload)
-    steps_evolve = args.evolve_steps or 20
+    print(json.dumps(measure_3d(p, args.evolve_steps or 20, args.steps, args.warmup)))
+
+
+def measure_3d(p, steps_evolve, K, W, warmup_steps=None):
+    """K timed whole 3-D solves of problem p with steps_evolve TVD-RK3 steps each, after W untimed
+    ones (of warmup_steps steps each, default steps_evolve); returns the bench record."""
+    import torch
+    import paper_2006_11945_gb300 as egb
     stream = torch.cuda.Stream()
     ctx = egb.Context(0, stream.cuda_stream)
     c21_d = torch.from_numpy(np.ascontiguousarray(p.c21)).cuda()
@@ -313,12 +332,12 @@ def run_egb3d(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     evolve_ms = []
 
-    def solve():
+    def solve(steps=steps_evolve):
         m = egb.egb_medium(ctx.h, (p.nx, p.ny, p.nz), (p.hx, p.hy, p.hz), tuple(p.origin), c21_d, rho_d, dim=3)
         s = egb.egb_source(ctx.h, m, tuple(p.xs), p.omegas, p.beam_width, p.n_theta, 0.0, n_phi=p.n_phi)
         with torch.cuda.stream(stream):
             ev0.record(stream)
-        egb.egb_evolve(ctx.h, s, steps_evolve, p.cfl)
+        egb.egb_evolve(ctx.h, s, steps, p.cfl)
         with torch.cuda.stream(stream):
             ev1.record(stream)
         egb.egb_superpose(ctx.h, s, u_d, cnt_d, T_d, A_d, kmax)
@@ -329,8 +348,8 @@ def run_egb3d(args):
         egb.egb_release(ctx.h, m)
         return info
 
-    for _ in range(args.warmup):
-        solve()
+    for _ in range(W):
+        solve(warmup_steps or steps_evolve)
     evolve_ms.clear()
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
@@ -338,7 +357,7 @@ def run_egb3d(args):
         t1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             t0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(K):
             info = solve()
         with torch.cuda.stream(stream):
             t1.record(stream)
@@ -348,22 +367,23 @@ def run_egb3d(args):
     launch_ms = float(np.mean(evolve_ms)) / (3 * steps_evolve)
     achieved = ALGO_BYTES_PER_CELL_UPDATE_3D * cells / 3.0 / (launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    print(json.dumps({
-        'metric': 'phase-space cell-updates/s', 'value': cells * steps_evolve * args.steps / (ms / 1e3),
-        'unit': 'cell-updates/s', 'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup,
-        'ms_per_step': ms / args.steps, 'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+    ctx.close()
+    return {
+        'metric': 'phase-space cell-updates/s', 'value': cells * steps_evolve * K / (ms / 1e3),
+        'unit': 'cell-updates/s', 'n_gpus': 1, 'steps': K, 'warmup': W,
+        'ms_per_step': ms / K, 'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': 'f32 (double-float tau and phase)', 'data': 'synthetic (seeded triclinic medium)',
         'config': {'workload': f'{p.name} {p.nx}^3 at {p.hx:g} m x {p.n_theta} polar x {p.n_phi} azimuth, '
                                f'{steps_evolve} of {p.steps} TVD-RK3 steps per solve, {len(p.freqs)} frequency',
                    'cells': cells, 'evolve_steps': steps_evolve, 'device_GB': info['device_bytes'] / 1e9,
                    'l2': 'state larger than L2, no flush'},
         'evolve_cell_updates_per_s': cells * steps_evolve / (float(np.mean(evolve_ms)) / 1e3),
+        'solves_per_s': K / (ms / 1e3),
         'roofline': {'bound': 'hbm', 'kernel': 'k_rk3_3d', 'achieved': achieved, 'peak': peak, 'unit': 'GB/s',
                      'frac': achieved / peak, 'traffic': None, 'peak_kind': peak_kind, 'launch_ms': launch_ms},
-        'gpu_launches': (2 + 4 + 3 * steps_evolve + 5) * args.steps,
+        'gpu_launches': (2 + 4 + 3 * steps_evolve + 5) * K,
         'clocks': clk.summary(),
-    }))
-    ctx.close()
+    }
 
 
 def run_batch(args):
@@ -441,6 +461,84 @@ def run_batch(args):
         'clocks': clk.summary(),
     }))
     ctx.close()
+
+
+def measure_batch_waves(ps, S, K, W):
+    """Uneven batched solves admitted in waves by free HBM (the library refuses a solve that does not
+    fit with EGB_E_NOMEM): each wave is every instance that fits beside the ones already admitted,
+    advanced S TVD-RK3 steps together by egb_evolve_batch (one persistent launch per stage over all
+    their work items), superposed and released before the next wave.  One bench step is one pass
+    over all instances; K timed after W untimed."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    stream = torch.cuda.Stream()
+    ctx = egb.Context(0, stream.cuda_stream)
+    outs = [(torch.empty((len(p.freqs), p.nz, p.nx, 2), dtype=torch.float32, device='cuda'),
+             torch.empty((p.nz, p.nx), dtype=torch.uint8, device='cuda'),
+             torch.empty((p.nz, p.nx, 8), dtype=torch.float64, device='cuda'),
+             torch.empty((p.nz, p.nx, 8), dtype=torch.float32, device='cuda')) for p in ps]
+    c21 = [torch.from_numpy(np.ascontiguousarray(p.c21)).cuda() for p in ps]
+    rho = [torch.from_numpy(np.ascontiguousarray(p.rho)).cuda() for p in ps]
+    waves = []
+
+    def one_pass():
+        i, sizes = 0, []
+        while i < len(ps):
+            wave = []
+            while i < len(ps):
+                p = ps[i]
+                try:
+                    m = egb.egb_medium(ctx.h, (p.nx, 1, p.nz), (p.hx, 1.0, p.hz), (p.origin[0], 0.0, p.origin[1]),
+                                       c21[i], rho[i])
+                except egb.EgbError as e:
+                    if e.status != egb.EGB_E_NOMEM or not wave:
+                        raise
+                    break
+                try:
+                    s = egb.egb_source(ctx.h, m, (p.xs[0], 0.0, p.xs[1]), p.omegas, p.beam_width, p.n_theta, 0.0)
+                except egb.EgbError as e:
+                    egb.egb_release(ctx.h, m)
+                    if e.status != egb.EGB_E_NOMEM or not wave:
+                        raise
+                    break
+                wave.append((i, m, s))
+                i += 1
+            egb.egb_evolve_batch(ctx.h, [s for _, _, s in wave], [S] * len(wave), ps[0].cfl)
+            for j, m, s in wave:
+                egb.egb_superpose(ctx.h, s, *outs[j], 8)
+                egb.egb_release(ctx.h, s)
+                egb.egb_release(ctx.h, m)
+            sizes.append(len(wave))
+        egb.egb_sync(ctx.h)
+        waves.append(sizes)
+
+    for _ in range(W):
+        one_pass()
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            one_pass()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+    ctx.close()
+    cells = sum(p.cells for p in ps)
+    return {
+        'metric': 'phase-space cell-updates/s', 'value': cells * S * K / (ms / 1e3), 'unit': 'cell-updates/s',
+        'n_gpus': 1, 'steps': K, 'warmup': W, 'ms_per_step': ms / K, 'higher_is_better': True,
+        'scaling': 'weak', 'dtype': 'f32 (double-float tau and phase)', 'data': 'synthetic (seeded TTI media)',
+        'config': {'workload': f'uneven batch: {len(ps)} instances of the 64-instance recipe (grids '
+                               f'{min(p.nx for p in ps)}^2-{max(p.nx for p in ps)}^2 at 5 m, '
+                               f'{min(p.n_theta for p in ps)}-{max(p.n_theta for p in ps)} angles, 1-4 '
+                               f'frequencies), admitted in waves by free HBM, {S} TVD-RK3 steps each, '
+                               f'every instance set up, superposed and released per step',
+                   'cells': cells, 'waves': waves[-1],
+                   'l2': 'state larger than L2, no flush'},
+        'solves_per_s': len(ps) * K / (ms / 1e3),
+        'timing': 'host wall clock around whole passes (setup, evolve, superpose, release)',
+        'gpu_launches': K * (len(ps) * (2 + 5 + 5) + 3 * S * len(waves[-1])),
+        'clocks': clk.summary(),
+    }
 
 
 def fp64_form(p, steps, device):
@@ -714,11 +812,21 @@ def serve_requests(duration, seed=4, rate=200.0, large_scale=1.0):
 def run_serve(args):
     """Serving measurement: arrivals for --serve-seconds, then drain what was admitted."""
     import torch
-    from paper_2006_11945_gb300.serve import Backend, serve
     torch.cuda.set_device(0)
-    reqs = serve_requests(args.serve_seconds, large_scale=args.serve_large_scale)
+    print(json.dumps(measure_serve(args.serve_seconds, args.serve_large_scale, args.serve_chunk,
+                                   args.serve_wall, args.serve_chunk_work, args.serve_max_chunk_work)))
+
+
+def measure_serve(seconds, large_scale, chunk, wall=None, chunk_work=4e9, max_chunk_work=2e10):
+    """Continuous batching on the Poisson request stream: arrivals for `seconds`, admitted by free
+    HBM; the loop then drains what was admitted, stopping at `wall` seconds (requests still on the
+    device are released and counted unfinished).  Returns the serving record."""
+    from paper_2006_11945_gb300.serve import Backend, serve
+    reqs = serve_requests(seconds, large_scale=large_scale)
     be = Backend(0)
-    st = serve(reqs, be, chunk_steps=args.serve_chunk, time_limit=args.serve_seconds)
+    with ClockSampler(0) as clk:
+        st = serve(reqs, be, chunk_steps=chunk, time_limit=seconds, wall_limit=wall, chunk_work=chunk_work,
+                   max_chunk_work=max_chunk_work)
     be.close()
     s = st.summary(len(reqs))
     small = [r.finished - r.arrival for r in st.completed if r.problem.name == 'vti_homogeneous']
@@ -728,12 +836,20 @@ def run_serve(args):
             s[f'{name}_p50_s'] = float(np.percentile(lat, 50))
             s[f'{name}_p99_s'] = float(np.percentile(lat, 99))
             s[f'{name}_completed'] = len(lat)
-    print(json.dumps({'metric': 'serving: solves/s and p50/p99 latency', 'value': s['solves_per_s'],
-                      'unit': 'solves/s', 'higher_is_better': True,
-                      'config': {'workload': f'Poisson 200 req/s for {args.serve_seconds} s, 50/50 '
-                                             f'64x64x64 VTI / {int(512 * args.serve_large_scale)}^2 TTI, '
-                                             f'1-8 frequencies', 'chunk_steps': args.serve_chunk},
-                      'serving': s}))
+    small_p = synthmedia.vti_homogeneous()
+    n_large = int(512 * large_scale) // 4 * 4
+    large_cu = n_large * n_large * max(16, int(256 * large_scale)) * synthmedia.tti_default_steps(
+        n_large, 2560.0 / n_large)
+    s['offered_per_s'] = len(reqs) / seconds
+    s['offered_cell_updates_per_s'] = s['offered_per_s'] * 0.5 * (small_p.cells * small_p.steps + large_cu)
+    return {'metric': 'serving: solves/s and p50/p99 latency', 'value': s['solves_per_s'],
+            'unit': 'solves/s', 'higher_is_better': True,
+            'config': {'workload': f'Poisson 200 req/s for {seconds:g} s, 50/50 64x64x64 VTI (150 steps) / '
+                                   f'{n_large}^2 TTI ({large_cu / n_large ** 2:.0f} cell-updates per node), '
+                                   f'1-8 frequencies, admission by free HBM, drain stopped at '
+                                   f'{wall if wall is not None else "completion"} s',
+                       'chunk_steps': chunk, 'chunk_work': chunk_work, 'max_chunk_work': max_chunk_work},
+            'serving': s, 'clocks': clk.summary()}
 
 
 def main():
@@ -753,6 +869,12 @@ def main():
     ap.add_argument('--serve-seconds', type=float, default=2.0)
     ap.add_argument('--serve-large-scale', type=float, default=1.0)
     ap.add_argument('--serve-chunk', type=int, default=60)
+    ap.add_argument('--serve-wall', type=float, default=None)
+    ap.add_argument('--serve-chunk-work', type=float, default=4e9,
+                    help='cell-updates a request advances per chunk (a small solve finishes in one)')
+    ap.add_argument('--serve-max-chunk-work', type=float, default=2e10,
+                    help='bound on the work of one chunk: admission shortest-work-first under it')
+    ap.add_argument('--no-sub', action='store_true', help='skip the 3-D, batch and serving sub-records')
     ap.add_argument('--evolve-steps', type=int, default=None)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--cpu-seconds', type=float, default=20.0)

@@ -65,7 +65,12 @@ typedef struct {
     int precision;      /* EGB_FP32_PHASE64: FP32 stencil/superposition with double-float tau and
                            phase; EGB_FP64: the plain all-FP64 form (comparison baseline) */
     int store_velocity; /* 1: characteristic velocities stored once per solve (the only mode) */
-    int checked;        /* reserved, 0 */
+    int wait_polls;     /* bound on the polls of each wait of the stencil on its own copies into
+                           shared memory (non-blocking polls about 32 ns apart);
+                           0 (or negative) = the default, about 2^22 polls with back-off (seconds).
+                           A wait that gives up latches EGB_E_TIMEOUT, returned by egb_sync: the
+                           stage launch leaves the solve's state undefined, the context stays
+                           usable.  Small values exist to exercise that path. */
 } egb_opts;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL for

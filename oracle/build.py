@@ -1,7 +1,8 @@
 """Compile the oracle's C stepping loop (test infrastructure only).
 
 ``python -m oracle.build`` or ``oracle.build.library()`` builds ``oracle/_build/liboracle.so`` from
-the 2-D and 3-D loops with gcc (-O2, OpenMP, no floating-point contraction) on the machine it runs on.
+the 2-D and 3-D loops with gcc (-O3, OpenMP, no floating-point contraction, so IEEE arithmetic in
+the order written) on the machine it runs on.
 """
 from __future__ import annotations
 
@@ -19,7 +20,7 @@ def build(force=False):
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < max(map(os.path.getmtime, _SRCS)):
         tmp = _OUT + f'.{os.getpid()}.tmp'
-        subprocess.check_call(['gcc', '-O2', '-fopenmp', '-ffp-contract=off', '-fPIC', '-shared',
+        subprocess.check_call(['gcc', '-O3', '-fopenmp', '-ffp-contract=off', '-fPIC', '-shared',
                                '-o', tmp] + _SRCS + ['-lm'])
         os.replace(tmp, _OUT)
     return _OUT

@@ -32,6 +32,11 @@ Angle-label differences are wrapped into [-pi, pi).
 Discretisation: Jiang & Peng's third-order HJ-WENO in each of x, z, theta, upwinded by the sign of
 the velocity component; Shu & Osher's TVD-RK3; dt = cfl / max_cells(|Vx|/hx + |Vz|/hz +
 |thetadot|/dtheta).
+
+Beside the labels the state carries alpha, the argument of the complex spreading continued through
+the evolution (superpose.track_branch, Eq. 26's square root past caustics): set from the initial
+data, re-lifted after every step whose count is a multiple of superpose.BRANCH_SAMPLE, and 'step',
+the number of steps taken.
 """
 from __future__ import annotations
 
@@ -41,6 +46,7 @@ import numpy as np
 
 from . import christoffel as _ch
 from . import medium as _md
+from . import superpose as _sp
 
 FIELDS = ('b', 'q', 'Th', 'tau')
 WENO_EPS_REL = 1e-6
@@ -85,7 +91,10 @@ class Setup:
         _, _, _, gs = _ch.source_quantities(self.a_s, self.theta)
         self.gs = gs
         dot = dx * gs[:, 0][:, None, None] + dz * gs[:, 1][:, None, None]
-        self.frozen = (r2 <= self.r0 * self.r0) | ((r2 <= self.R_sigma * self.R_sigma) & (dot < 0.0))
+        # a cell on the closest-approach line (d . g_s at rounding level, e.g. diagonal directions of
+        # an isotropic source on a node) belongs to the leaving half, as in 3-D
+        approach = (dot < 0.0) & (dot * dot > 1e-24 * r2)
+        self.frozen = (r2 <= self.r0 * self.r0) | ((r2 <= self.R_sigma * self.R_sigma) & approach)
         rate = (np.abs(self.vel['Vx']) / self.hx + np.abs(self.vel['Vz']) / self.hz
                 + np.abs(self.vel['thetadot']) / self.dth)
         self.max_rate = float(rate.max())
@@ -112,7 +121,10 @@ class Setup:
         tau = (np.sin(th) * X + np.cos(th) * Z) / v
         q = np.zeros_like(b)
         q[:, GHOST:-GHOST, GHOST:-GHOST][self.frozen] = 1.0
-        return {'b': b, 'q': q, 'Th': np.broadcast_to(th, b.shape).copy(), 'tau': tau}
+        st = {'b': b, 'q': q, 'Th': np.broadcast_to(th, b.shape).copy(), 'tau': tau}
+        st['alpha'] = _sp.track_branch(self, interior_state(st, self))
+        st['step'] = 0
+        return st
 
 
 def _velocity_planes(args):
@@ -249,13 +261,32 @@ def evolve(problem, steps=None, cfl=None, S=None, state=None, backend='c'):
     dt = S.dt(cfl)
     if state is None:
         state = S.initial_state()
-    if backend == 'c':
-        return S, _evolve_c(S, state, dt, steps), dt
-    for _ in range(steps):
-        state = rk3_step(state, S, dt)
-    return S, state, dt
+    fields = {f: state[f] for f in FIELDS}
+    if 'alpha' in state:
+        alpha, step = state['alpha'], int(state['step'])
+    else:
+        alpha, step = _sp.track_branch(S, interior_state(fields, S)), 0
+    done = 0
+    while done < steps:
+        n = min(steps - done, _sp.BRANCH_SAMPLE - step % _sp.BRANCH_SAMPLE)
+        if backend == 'c':
+            fields = _evolve_c(S, fields, dt, n)
+        else:
+            for _ in range(n):
+                fields = rk3_step(fields, S, dt)
+        done += n
+        step += n
+        if step % _sp.BRANCH_SAMPLE == 0:
+            alpha = _sp.track_branch(S, interior_state(fields, S), alpha)
+    out = dict(fields)
+    out['alpha'], out['step'] = alpha, step
+    return S, out, dt
 
 
 def interior_state(state, S):
-    """Interior (unpadded) copies of the four fields, shape (n_theta, nz, nx)."""
-    return {f: _interior(state[f], S).copy() for f in FIELDS}
+    """Interior (unpadded) copies of the four fields, shape (n_theta, nz, nx), and of the continued
+    spreading argument alpha when the state has one."""
+    out = {f: _interior(state[f], S).copy() for f in FIELDS}
+    if 'alpha' in state:
+        out['alpha'] = state['alpha'].copy()
+    return out

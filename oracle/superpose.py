@@ -24,9 +24,18 @@ Reading taken here (the paper's Eqs. 24 and 28-33 are garbled or isotropic-only)
   (|beam| = 1/e at w0; the complex initial data of Eq. 24).  With dx = (d_x, d_z) and
   dp = p (pdot . dx) + dp/dtheta d_theta, M [dx, V] = [dp, pdot] gives the Cartesian Hessian
   (Eq. 25's M = B C^-1) and J = dx x V the complex spreading (det C of Eq. 26).
-* Amplitude (Eq. 26 with the elastic transport div(rho U^2 V) = 0): sigma sqrt(rho_s |V_s| / (rho J))
-  on the principal branch, sigma = -1 where arg J < -1e-3 (J has crossed the negative real axis at a
-  caustic: KMAH index 1; near the source J is close to the positive real axis and sigma = +1).
+* Amplitude (Eq. 26 with the elastic transport div(rho U^2 V) = 0): rho_s |V_s| / (rho J) under a
+  square root continued along the ray.  J never vanishes for the complex beam family (its real and
+  imaginary parts, the offset and take-off families, never vanish together), and its argument grows
+  by pi at every caustic (KMAH index), so the principal root is right only up to the first
+  crossing of the negative real axis.  The continued argument is followed per phase cell through
+  the pseudo-time evolution (`track_branch`): alpha, the argument of the reference spreading
+  J_ref = J_b + i J_T / w0 (offset family plus the take-off family scaled by 1/w0), is re-lifted
+  every BRANCH_SAMPLE steps to the value of the current principal argument nearest to it.  With the
+  labels fixed, the homotopy from the initial straight-ray data (no caustic) to the steady state
+  carries alpha continuously onto the argument continued along the ray.  At a beam centre
+  k = rint((alpha_c - arg J_ref) / 2 pi) and sigma = (-1)^k multiplies the principal root: every
+  frequency's J = J_b + kappa J_T has the sign of Im J_ref, so the same k continues all of them.
 * Weight (the calibrated Psi_0 of Eqs. 30-33): i c_ref^2 / (4 pi v_s(vartheta)^2) times the
   take-off measure |d vartheta_c / d theta| dtheta, so that a homogeneous isotropic medium gives
   the 2-D Helmholtz Green's function (i/4) H0^(1)(kr) as kr -> inf; the output is rho_s c_ref^2
@@ -49,7 +58,8 @@ import numpy as np
 from . import christoffel as _ch
 
 
-KMAH_ARG = 1e-3
+# steps between two samples of the continued argument of the complex spreading (track_branch)
+BRANCH_SAMPLE = 9
 
 
 def _wrap(d):
@@ -74,19 +84,71 @@ def _grad_theta(f, dth, wrap):
     return d / (2 * dth)
 
 
+def _label_gradients(S, b, Th):
+    return dict(bx=_grad_axis(b, S.hx, 2, False), bz=_grad_axis(b, S.hz, 1, False),
+                bt=_grad_theta(b, S.dth, False),
+                Tx=_grad_axis(Th, S.hx, 2, True), Tz=_grad_axis(Th, S.hz, 1, True),
+                Tt=_grad_theta(Th, S.dth, True))
+
+
+def _families(et, k1, k2):
+    """Phase-space perturbations (last axis 3) with (db, dvartheta) = (1, 0) and (0, 1) that keep the
+    ray direction e_t: d_b = (k2 x e_t) / D, d_T = (e_t x k1) / D, D = e_t . (k1 x k2).
+
+    D is the orientation of the label coordinates (b, vartheta, tau): e_t is parallel to
+    k1 x k2, and D / |e_t|^2 = det[grad b, grad vartheta, grad tau].  The label map is one-to-one on
+    the source tube and equals the straight-ray data there at the start, where D < 0, so D < 0
+    throughout; a positive discrete D (centred differences of under-resolved labels) is taken as
+    -|D|, which keeps J's orientation (a sign flip of D alone would multiply the amplitude by
+    +-i) and makes the argument of J continuous where the discrete D passes through zero."""
+    D = -np.abs(np.einsum('...i,...i->...', et, np.cross(k1, k2)))
+    return np.cross(k2, et) / D[..., None], np.cross(et, k1) / D[..., None]
+
+
+def reference_arg(S, b, Th):
+    """Per cell: principal argument of J_ref = J_b + i J_T / w0, the complex spreading dx x V of the
+    offset family (J_b) plus the take-off family scaled by the beam width (J_T), from the centred
+    label gradients; NaN where the level-set Jacobian is singular."""
+    G = _label_gradients(S, b, Th)
+    et = np.stack([S.vel['Vx'], S.vel['Vz'], S.vel['thetadot']], -1)
+    k1 = np.stack([G['bx'], G['bz'], G['bt']], -1)
+    k2 = np.stack([G['Tx'], G['Tz'], G['Tt']], -1)
+    with np.errstate(divide='ignore', invalid='ignore'):
+        d_b, d_T = _families(et, k1, k2)
+        Jb = d_b[..., 0] * S.vel['Vz'] - d_b[..., 1] * S.vel['Vx']
+        JT = d_T[..., 0] * S.vel['Vz'] - d_T[..., 1] * S.vel['Vx']
+        a = np.arctan2(JT / S.p.beam_width, Jb)
+    return np.where(np.isfinite(Jb) & np.isfinite(JT), a, np.nan)
+
+
+def lift_branch(alpha, a):
+    """The value a + 2 pi k (k integer) nearest to alpha; alpha itself where a is undefined."""
+    lifted = a + 2.0 * np.pi * np.rint((alpha - a) / (2.0 * np.pi))
+    return np.where(np.isfinite(a), lifted, alpha)
+
+
+def track_branch(S, lab, alpha=None):
+    """One sample of the continued argument of the complex spreading on every cell (interior
+    labels b, vartheta of shape (n_theta, nz, nx)): alpha lifted to the current principal argument,
+    or that argument itself when alpha is None (the initial data, which has no caustic)."""
+    a = reference_arg(S, lab['b'], lab['Th'])
+    if alpha is None:
+        return np.where(np.isfinite(a), a, 0.0)
+    return lift_branch(alpha, a)
+
+
 def beam_fields(S, lab):
     """Frequency-independent per-cell quantities of the superposition (all float64)."""
     b, q, Th, tau = lab['b'], lab['q'], lab['Th'], lab['tau']
     vs, _, Vsn, _ = _ch.source_quantities(S.a_s, Th)
-    return dict(
-        b=b, tau=tau, vs=vs, Vsn=Vsn, Th=Th,
-        bx=_grad_axis(b, S.hx, 2, False), bz=_grad_axis(b, S.hz, 1, False),
-        bt=_grad_theta(b, S.dth, False),
-        Tx=_grad_axis(Th, S.hx, 2, True), Tz=_grad_axis(Th, S.hz, 1, True),
-        Tt=_grad_theta(Th, S.dth, True),
-        # rays whose labels came from the source manifold and that have left it
-        flag=(q > 0.5) & ~S.frozen,
-    )
+    F = dict(b=b, tau=tau, vs=vs, Vsn=Vsn, Th=Th,
+             # rays whose labels came from the source manifold and that have left it
+             flag=(q > 0.5) & ~S.frozen)
+    F.update(_label_gradients(S, b, Th))
+    # the continued argument, sampled once more on the labels being superposed; labels given without
+    # one (closed-form steady states of caustic-free media) take the principal argument
+    F['alpha'] = track_branch(S, lab, lab.get('alpha'))
+    return F
 
 
 def _interp(a, i0, i1, t):
@@ -112,7 +174,7 @@ def crossings(S, lab, F, axis):
     c0 = (k, iz, ix)
     t = b[c0] / (b[c0] - b[c1])
     out = dict(k=k, iz=iz, ix=ix, t=t)
-    names = ('tau', 'bx', 'bz', 'bt', 'Tx', 'Tz', 'Tt')
+    names = ('tau', 'bx', 'bz', 'bt', 'Tx', 'Tz', 'Tt', 'alpha')
     for nm in names:
         out[nm] = _interp(F[nm], c0, c1, t)
     for nm in ('Vx', 'Vz', 'thetadot', 'pdx', 'pdz', 'v'):
@@ -147,9 +209,7 @@ def beam_centres(S, lab, F, axis, omega, beam_width):
     et = np.stack([c['Vx'], c['Vz'], c['thetadot']], -1)
     k1 = np.stack([c['bx'], c['bz'], c['bt']], -1)
     k2 = np.stack([c['Tx'], c['Tz'], c['Tt']], -1)
-    D = np.einsum('ni,ni->n', et, np.cross(k1, k2))
-    d_b = np.cross(k2, et) / D[:, None]
-    d_T = np.cross(et, k1) / D[:, None]
+    d_b, d_T = _families(et, k1, k2)
     vs, _, Vsn, _ = _ch.source_quantities(S.a_s, c['Th'])
     kappa = 2j * Vsn / (omega * beam_width ** 2)
     d = d_b + kappa[:, None] * d_T
@@ -163,10 +223,12 @@ def beam_centres(S, lab, F, axis, omega, beam_width):
     J_theta = d_T[:, 0] * V[:, 1] - d_T[:, 1] * V[:, 0]
     Mxx = (dp[:, 0] * V[:, 1] - pdot[:, 0] * dx[:, 1]) / J
     Mzz = (-dp[:, 1] * V[:, 0] + pdot[:, 1] * dx[:, 0]) / J
-    # KMAH index 1: J leaves the upper half plane through the negative real axis at the first
-    # caustic, where the principal square root jumps; sigma = -1 once arg J < -KMAH_ARG.  Near the
-    # source J is close to the positive real axis (take-off part ~ 0) and sigma stays +1.
-    sigma = np.where(np.angle(J) < -KMAH_ARG, -1.0, 1.0)
+    # Square root continued along the ray: the continued argument alpha of J_ref at the centre
+    # fixes the sheet, k = rint((alpha - arg J_ref) / 2 pi), sigma = (-1)^k on the principal root.
+    Jb = d_b[:, 0] * V[:, 1] - d_b[:, 1] * V[:, 0]
+    a_ref = np.arctan2(J_theta / S.p.beam_width, Jb)
+    k = np.rint((c['alpha'] - a_ref) / (2.0 * np.pi))
+    sigma = np.where(np.mod(k, 2.0) == 0.0, 1.0, -1.0)
     amp = sigma * np.sqrt(S.rho_s * Vsn / (c['rho'] * J))
     # Take-off measure along the line times the row/column blend.  Along a row the beam centre moves
     # with theta as dx_c/dtheta = -b_theta/b_x, so d vartheta_c/dtheta = vartheta_theta -
@@ -188,6 +250,14 @@ def beam_centres(S, lab, F, axis, omega, beam_width):
     coef = np.where(ok, coef, 0.0)
     M = np.where(ok, M, 0.0)
     return c, dict(coef=coef, M=M, p=pl)
+
+
+def _scatter_add(u, flat, vals):
+    """u.flat[flat] += vals, summing repeated indices (np.add.at, written with bincount)."""
+    n = u.size
+    f, v = flat.ravel(), vals.ravel()
+    u += (np.bincount(f, weights=v.real, minlength=n)
+          + 1j * np.bincount(f, weights=v.imag, minlength=n)).reshape(u.shape)
 
 
 def green(S, lab, omegas, beam_width):
@@ -223,15 +293,19 @@ def green(S, lab, omegas, beam_width):
                                    + 0.5 * Mc * delta ** 2))
             contrib = bc['coef'][:, None] * ph
             if axis == 2:
-                np.add.at(u, (c['iz'][:, None], np.arange(S.nx)[None, :]), contrib)
+                _scatter_add(u, c['iz'][:, None] * S.nx + np.arange(S.nx)[None, :], contrib)
             else:
-                np.add.at(u, (np.arange(S.nz)[None, :], c['ix'][:, None]), contrib)
+                _scatter_add(u, np.arange(S.nz)[None, :] * S.nx + c['ix'][:, None], contrib)
         out.append(u)
     return np.stack(out)
 
 
-def arrivals(S, lab, kmax=8):
-    """count (nz, nx) uint8, T (nz, nx, kmax) float64, A (nz, nx, kmax) float64, overflow flag."""
+def arrivals(S, lab, kmax=8, kmah=False):
+    """count (nz, nx) uint8, T (nz, nx, kmax) float64, A (nz, nx, kmax) float64, overflow flag;
+    with kmah=True also M (nz, nx, kmax) int, each arrival's KMAH index: the number of caustics its
+    ray has passed, floor(alpha / pi) of the continued argument alpha of the complex spreading,
+    interpolated at the crossing like T (it grows by pi at every caustic; 0 < alpha < pi on the
+    straight-ray initial data downstream of the source)."""
     F = beam_fields(S, lab)
     v_r = S.vel['v']
     rho_r = S.rho[None, :, :]
@@ -241,8 +315,8 @@ def arrivals(S, lab, kmax=8):
     with np.errstate(divide='ignore'):
         Acell = S.c_ref ** 2 * np.sqrt(S.rho_s / rho_r) / (
             v_r * np.sqrt(8 * np.pi * F['Vsn'] * np.abs(F['bt'])))
-    b, tau, flag = F['b'], F['tau'], F['flag']
-    bn, taun, flagn, An = (np.roll(a, -1, axis=0) for a in (b, tau, flag, Acell))
+    b, tau, flag, alpha = F['b'], F['tau'], F['flag'], F['alpha']
+    bn, taun, flagn, An, alphan = (np.roll(a, -1, axis=0) for a in (b, tau, flag, Acell, alpha))
     cross = flag & flagn & ((b >= 0) != (bn >= 0))
     nth, nz, nx = b.shape
     count = np.zeros((nz, nx), np.uint8)
@@ -259,6 +333,8 @@ def arrivals(S, lab, kmax=8):
         raise FloatingPointError(
             'arrival at node (%d, %d), angle cell %d lies on a cell with d b / d theta = 0: '
             'its geometrical amplitude is undefined' % (izs[bad], ixs[bad], ks[bad]))
+    Mval = np.floor((alpha[ks, izs, ixs] + t * (alphan[ks, izs, ixs] - alpha[ks, izs, ixs])) / np.pi)
+    M = np.zeros((nz, nx, kmax), np.int64)
     order = np.lexsort((ks, Tval, ixs, izs))
     per_node = {}
     for j in order:
@@ -270,6 +346,9 @@ def arrivals(S, lab, kmax=8):
         count[iz, ix] = len(js)
         T[iz, ix, :len(js)] = Tval[js]
         A[iz, ix, :len(js)] = Aval[js]
+        M[iz, ix, :len(js)] = Mval[js]
+    if kmah:
+        return count, T, A, overflow, M
     return count, T, A, overflow
 
 

@@ -61,6 +61,7 @@ import numpy as np
 
 from . import christoffel as _ch
 from . import medium as _md
+from . import superpose as _SP
 
 GHOST = 2
 WENO_EPS_REL = 1e-6
@@ -273,7 +274,7 @@ def green_rows(Z, H, omegas, beam_width, F=None):
         M = np.where(ok, M, 0.0)
         Mc = M.real + 1j * np.maximum(M.imag, 0.0)
         ph = np.exp(1j * om * (q['tau'][:, None] + px[:, None] * delta + 0.5 * Mc[:, None] * delta ** 2))
-        np.add.at(out[w], (r[:, None], np.arange(nx)[None, :]), coef[:, None] * ph)
+        _SP._scatter_add(out[w], r[:, None] * nx + np.arange(nx)[None, :], coef[:, None] * ph)
     return out
 
 

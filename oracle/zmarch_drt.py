@@ -28,6 +28,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import christoffel as _ch
+from . import superpose as _SP
 from . import zmarch as _zm
 
 QFIELDS = ('x1', 't1', 'x2', 't2')
@@ -134,7 +135,7 @@ def green_rows_q(Z, H, Qh, omegas, beam_width):
         M = np.where(ok, M, 0.0)
         Mc = M.real + 1j * np.maximum(M.imag, 0.0)
         ph = np.exp(1j * om * (q['tau'][:, None] + px[:, None] * delta + 0.5 * Mc[:, None] * delta ** 2))
-        np.add.at(out[w], (r[:, None], np.arange(nx)[None, :]), coef[:, None] * ph)
+        _SP._scatter_add(out[w], r[:, None] * nx + np.arange(nx)[None, :], coef[:, None] * ph)
     return out
 
 

@@ -39,7 +39,7 @@ class EgbError(RuntimeError):
 
 
 class egb_opts(ctypes.Structure):
-    _fields_ = [('precision', ctypes.c_int), ('store_velocity', ctypes.c_int), ('checked', ctypes.c_int)]
+    _fields_ = [('precision', ctypes.c_int), ('store_velocity', ctypes.c_int), ('wait_polls', ctypes.c_int)]
 
 
 class egb_zmarch_info(ctypes.Structure):
@@ -119,10 +119,10 @@ def _check(ctx_handle, status):
 
 # ---- thin functions with the C names ------------------------------------------------------------
 
-def egb_create(device: int = 0, stream: int = 0, precision: int = EGB_FP32_PHASE64):
+def egb_create(device: int = 0, stream: int = 0, precision: int = EGB_FP32_PHASE64, wait_polls: int = 0):
     lib = load()
     h = ctypes.c_void_p()
-    opts = egb_opts(precision, 1, 0)
+    opts = egb_opts(precision, 1, wait_polls)
     st = lib.egb_create(ctypes.byref(h), device, ctypes.c_void_p(stream or None), ctypes.byref(opts))
     if st != EGB_OK:
         raise EgbError(st, 'egb_create failed (no CUDA device?)')
@@ -223,8 +223,8 @@ class SolveResult:
 class Context:
     """Owns one egb context on a CUDA stream (an int cudaStream_t handle; 0 = legacy default)."""
 
-    def __init__(self, device=0, stream=0, precision=EGB_FP32_PHASE64):
-        self.h = egb_create(device, stream, precision)
+    def __init__(self, device=0, stream=0, precision=EGB_FP32_PHASE64, wait_polls=0):
+        self.h = egb_create(device, stream, precision, wait_polls)
 
     def close(self):
         if self.h is not None:

@@ -1,4 +1,5 @@
 // C ABI of libegb: contexts, media and solves (declared in include/egb.h).
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +56,18 @@ size_t free_bytes() {
     return fr;
 }
 
+// Device allocation of a medium or solve of context c.  With EGB_FAIL_ALLOC=n set in the
+// environment when the context was created, the allocation after the first n fails the way
+// cudaMalloc does when device memory is short (host-side fault injection for the error paths).
+template <class T>
+static cudaError_t ctx_malloc(Ctx *c, T **p, size_t bytes) {
+    if (c->fail_alloc >= 0 && c->fail_alloc-- == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc((void **)p, bytes);
+}
+
 void free_solve(Solve *s) {
     for (auto &p : s->state) cudaFree(p);
     for (auto &p : s->state64) cudaFree(p);
@@ -65,6 +78,7 @@ void free_solve(Solve *s) {
     cudaFree(s->gs64);
     tma_release(*s);
     cudaFree(s->src);
+    cudaFree(s->alpha);
     cudaFree(s->scratch);
     delete s;
 }
@@ -177,11 +191,11 @@ egb_status source3d(egb_ctx *c, uint64_t mid, Medium *m, const double xs[3], int
     }
     cudaError_t e = cudaSuccess;
     for (auto &p : s->state)
-        if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
-    if (e == cudaSuccess) e = cudaMalloc(&s->vel, cells * 9 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&s->frozen, cells);
-    if (e == cudaSuccess) e = cudaMalloc(&s->gs64, sizeof(double) * 3 * nth * nph);
-    if (e == cudaSuccess) e = cudaMalloc(&s->src, 32 * 4);
+        if (e == cudaSuccess) e = ctx_malloc(c, &p, state_b);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->vel, cells * 9 * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->frozen, cells);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->gs64, sizeof(double) * 3 * nth * nph);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->src, 32 * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_solve3d(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
     float *d_rate = nullptr;
     e = cudaMalloc(&d_rate, 4);
@@ -260,6 +274,7 @@ egb_status egb_create(egb_ctx **out, int device, void *cuda_stream, const egb_op
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     c->opts = opts ? *opts : egb_opts{EGB_FP32_PHASE64, 1, 0};
+    if (const char *f = std::getenv("EGB_FAIL_ALLOC")) c->fail_alloc = std::strtol(f, nullptr, 10);
     DeviceGuard dg(device);
     if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
@@ -325,12 +340,12 @@ egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], co
     m->bytes = nodes * 4 * (21 * (dim + 1) + 1);
     if (m->bytes + (64u << 20) > free_bytes()) { delete m; return fail(c, EGB_E_NOMEM, "medium needs %zu bytes", m->bytes); }
     cudaError_t e = cudaSuccess;
-    e = cudaMalloc(&m->a, nodes * 21 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&m->dadx, nodes * 21 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&m->dadz, nodes * 21 * 4);
-    if (e == cudaSuccess && dim == 3) e = cudaMalloc(&m->dady, nodes * 21 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&m->rho, nodes * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&m->c21, nodes * 21 * 4);
+    e = ctx_malloc(c, &m->a, nodes * 21 * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &m->dadx, nodes * 21 * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &m->dadz, nodes * 21 * 4);
+    if (e == cudaSuccess && dim == 3) e = ctx_malloc(c, &m->dady, nodes * 21 * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &m->rho, nodes * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &m->c21, nodes * 21 * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_medium(m); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the medium"); }
     const float *dc = c21, *dr = rho;
     float *tc = nullptr, *tr = nullptr;
@@ -399,6 +414,7 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     s->zs = xs[2];
     s->r0 = r0 > 0 ? r0 : 2.0 * (m->hx > m->hz ? m->hx : m->hz);
     s->w0 = beam_width;
+    s->wait_polls = c->opts.wait_polls > 0 ? (uint32_t)c->opts.wait_polls : 0u;
     s->omega.assign(omega, omega + n_omega);
     size_t cells = (size_t)nth * g.nx * g.nz;
     size_t state_b = (size_t)NFIELD * g.field * 4;
@@ -408,33 +424,34 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     auto cached = s->fp64 ? m->vel_cache.end() : m->vel_cache.find(nth);
     bool reuse = cached != m->vel_cache.end();
     s->bytes = (s->fp64 ? state_b + 3 * state64_b : 3 * state_b) + (reuse ? 0 : cells * 6 * 4) + velp_b + cells +
-               (24 + 4 * nth) * 4;
+               cells * 4 + (24 + 4 * nth) * 4;
     if (s->bytes + (256u << 20) > free_bytes()) {
         delete s;
         return fail(c, EGB_E_NOMEM, "solve needs %zu bytes of device memory", (size_t)(s->bytes));
     }
     cudaError_t e = cudaSuccess;
     if (s->fp64) {
-        e = cudaMalloc(&s->state[0], state_b);
+        e = ctx_malloc(c, &s->state[0], state_b);
         for (auto &p : s->state64)
-            if (e == cudaSuccess) e = cudaMalloc(&p, state64_b);
-        if (e == cudaSuccess) e = cudaMalloc(&s->velp64, velp_b);
+            if (e == cudaSuccess) e = ctx_malloc(c, &p, state64_b);
+        if (e == cudaSuccess) e = ctx_malloc(c, &s->velp64, velp_b);
         if (e == cudaSuccess) e = cudaMemsetAsync(s->velp64, 0, velp_b, c->stream);
     } else {
         for (auto &p : s->state)
-            if (e == cudaSuccess) e = cudaMalloc(&p, state_b);
-        if (e == cudaSuccess) e = cudaMalloc(&s->velp, velp_b);
+            if (e == cudaSuccess) e = ctx_malloc(c, &p, state_b);
+        if (e == cudaSuccess) e = ctx_malloc(c, &s->velp, velp_b);
         if (e == cudaSuccess) e = cudaMemsetAsync(s->velp, 0, velp_b, c->stream);
     }
     if (reuse) {
         s->vel = cached->second.vel;
         s->vel_shared = true;
     } else if (e == cudaSuccess) {
-        e = cudaMalloc(&s->vel, cells * 6 * 4);
+        e = ctx_malloc(c, &s->vel, cells * 6 * 4);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&s->frozen, cells);
-    if (e == cudaSuccess) e = cudaMalloc(&s->gs64, sizeof(double) * 2 * s->g.nth);
-    if (e == cudaSuccess) e = cudaMalloc(&s->src, (24 + 4 * nth) * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->frozen, cells);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->gs64, sizeof(double) * 2 * s->g.nth);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->src, (24 + 4 * nth) * 4);
+    if (e == cudaSuccess) e = ctx_malloc(c, &s->alpha, cells * 4);
     if (e != cudaSuccess) { cudaGetLastError(); free_solve(s); return fail(c, EGB_E_NOMEM, "cudaMalloc failed for the solve"); }
     if (!s->fp64) {
         e = tma_prepare(*s);
@@ -465,6 +482,9 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
         if (e == cudaSuccess) e = launch_init_state(*s, c->stream);
         if (e == cudaSuccess) e = launch_zero_frozen_velocity(*s, c->stream);
     }
+    // first sample of the continued spreading argument, on the initial labels
+    if (e == cudaSuccess && s->fp64) e = fp64_to_fp32_state(*s, c->stream);
+    if (e == cudaSuccess) e = launch_track_branch(*s, s->state[s->fp64 ? 0 : s->cur], true, c->stream);
     float rate = 0, cref = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&rate, d_rate, 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cref, s->src + 22, 4, cudaMemcpyDeviceToHost, c->stream);
@@ -523,6 +543,11 @@ egb_status egb_evolve(egb_ctx *c, egb_solve_id sid, int steps, double cfl) {
     if (s->fp64) {
         for (int i = 0; i < steps; ++i) {
             cudaError_t e = launch_rk3_step64(*s, s->dt, c->stream);
+            // sample the continued spreading argument from the FP32 rounding of the state
+            if (e == cudaSuccess && (s->steps + i + 1) % BRANCH_SAMPLE == 0) {
+                e = fp64_to_fp32_state(*s, c->stream);
+                if (e == cudaSuccess) e = launch_track_branch(*s, s->state[0], false, c->stream);
+            }
             if (e != cudaSuccess) return cuda_fail(c, e, "evolve launch");
         }
     } else {

@@ -27,6 +27,9 @@ constexpr int XPAD = 4;
 constexpr int ZPAD = 2;
 constexpr int NFIELD = 5;
 constexpr int KC = 16;  // beam centres kept per grid line and angle
+// Steps between two samples of the continued argument of the complex spreading (the sheet of the
+// amplitude's square root past caustics): a sample follows every step whose count is a multiple.
+constexpr int BRANCH_SAMPLE = 9;
 
 struct Grid2D {
     int nx, nz, nth;
@@ -123,11 +126,13 @@ struct Solve {
     double *state64[3] = {nullptr, nullptr, nullptr};  // [4 fields] Yx, Yz, vartheta, tau (FP64 form)
     double *velp64 = nullptr;                           // [3] padded Vx, Vz, thetadot (FP64 form)
     float *src = nullptr;   // source block: a_s[21], rho_s, c_ref, then [nth] x (psx, psz)
+    float *alpha = nullptr; // [nth][nz][nx] continued argument of the reference complex spreading
     float *scratch = nullptr;  // superposition scratch (lazily sized)
     size_t scratch_bytes = 0;
     double max_rate = 0, dt = 0, c_ref = 0;
     int steps = 0;
     size_t bytes = 0;
+    uint32_t wait_polls = 0;  // bound of the stencil's waits on its copies (0: the default)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -196,6 +201,9 @@ struct Ctx {
     // theta chunk chosen by the stencil autotuner, per grid shape (nx, nz, n_theta): later solves
     // of the same shape reuse it instead of timing the candidates again
     std::unordered_map<uint64_t, int> tuned_chunk;
+    // host-side fault injection (EGB_FAIL_ALLOC at egb_create): the number of device allocations of
+    // media and solves that succeed before one fails; -1 when off
+    long fail_alloc = -1;
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -214,6 +222,8 @@ void tma_set_chunk(Solve &sv, int chunk);
 cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s);
 cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
                          cudaStream_t cap);
+// One sample of the continued spreading argument from the padded FP32 state st (init: first sample).
+cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cudaStream_t s);
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 size_t superpose_scratch_bytes(const Solve &sv);

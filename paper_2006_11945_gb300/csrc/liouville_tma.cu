@@ -53,6 +53,7 @@ struct StageDesc {
     float dt, coef, ihx, ihz, idth;
     float eps[4];
     int tiles_x, tiles_z, chunk, items, item_begin;
+    uint32_t polls;  // limit of each bounded wait on a copy of this solve's planes
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -75,11 +76,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^22 polls (seconds), returning false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i) {
-        if (mbar_try_wait(b, parity)) return true;
-        if (i > 16) __nanosleep(128);
+// Non-blocking poll: true once the phase with this parity has completed.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls, returning false.  The default bound (2^22 polls with
+// back-off) is seconds.  A caller-set bound uses non-blocking polls 32 ns apart, so that a small
+// bound gives up while a copy is still in flight.
+constexpr uint32_t DEFAULT_POLLS = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity, uint32_t limit = DEFAULT_POLLS) {
+    if (limit >= DEFAULT_POLLS) {
+        for (uint32_t i = 0; i < limit; ++i) {
+            if (mbar_try_wait(b, parity)) return true;
+            if (i > 16) __nanosleep(128);
+        }
+        return false;
+    }
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_test_wait(b, parity)) return true;
+        __nanosleep(32);
     }
     return false;
 }
@@ -156,7 +178,9 @@ __device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5]
     return weno3_2(d, up, eps2);
 }
 
-template <int STAGE>
+// BOUNDED: the waits on this launch's copies use the solves' caller-set poll bound (egb_opts.wait_polls)
+// instead of the default one; a separate instantiation keeps the default kernel free of it.
+template <int STAGE, bool BOUNDED>
 __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
     k_rk3_tma(const StageDesc *__restrict__ D, int nsolves, int total_items, unsigned *err) {
     using namespace tma;
@@ -223,12 +247,17 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
             for (int j = 0; j < min(RING, nplanes); ++j) issue(j);
             for (int j = 0; j < min(RING2, kn); ++j) issue2(j);
         }
+        // A slot's parity flips and its pending bit clears only once its copy has been seen to
+        // land: after a wait that gives up, the drain below still waits for that copy.
+        const uint32_t polls = BOUNDED ? A.polls : DEFAULT_POLLS;
         bool ok = true;
         for (int j = 0; j < 4 && ok; ++j) {
             int s = j % RING;
-            ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u);
-            phase ^= 1u << s;
-            if (tid == 0) pending &= ~(1u << s);
+            ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u, polls);
+            if (ok) {
+                phase ^= 1u << s;
+                if (tid == 0) pending &= ~(1u << s);
+            }
         }
         const int iz = z0 + tz;
         const int ixa = x0 + 2 * tx;
@@ -237,13 +266,21 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
         for (int kk = 0; kk < kn; ++kk, sb = (sb + 1 == RING ? 0 : sb + 1)) {
             {
                 int s = sb + 4 >= RING ? sb + 4 - RING : sb + 4;
-                if (ok) ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u);
-                phase ^= 1u << s;
-                if (tid == 0) pending &= ~(1u << s);
+                if (ok) {
+                    ok = mbar_wait_bounded(bar + s, (phase >> s) & 1u, polls);
+                    if (ok) {
+                        phase ^= 1u << s;
+                        if (tid == 0) pending &= ~(1u << s);
+                    }
+                }
                 int s2 = kk % RING2;
-                if (ok) ok = mbar_wait_bounded(bar2 + s2, (phase2 >> s2) & 1u);
-                phase2 ^= 1u << s2;
-                if (tid == 0) pending2 &= ~(1u << s2);
+                if (ok) {
+                    ok = mbar_wait_bounded(bar2 + s2, (phase2 >> s2) & 1u, polls);
+                    if (ok) {
+                        phase2 ^= 1u << s2;
+                        if (tid == 0) pending2 &= ~(1u << s2);
+                    }
+                }
             }
             if (!ok) atomicOr(&abort_flag, 1);
             const int k = k0 + kk;
@@ -335,7 +372,8 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
         if (abort_flag) break;
     }
     if (abort_flag) {
-        // latch the timeout and drain the copies this CTA still has in flight (bounded)
+        // latch the timeout and drain the copies this CTA still has in flight (with the default
+        // bound: they were issued correctly and land, so the CTA never leaves with one pending)
         if (tid == 0) {
             atomicOr(err, DeviceErrors::TIMEOUT);
             for (int s = 0; s < RING; ++s)
@@ -423,9 +461,12 @@ cudaError_t tma_prepare(Solve &sv) {
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
     if (!attr_done) {
-        cudaFuncSetAttribute(k_rk3_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
-        cudaFuncSetAttribute(k_rk3_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
-        cudaFuncSetAttribute(k_rk3_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
+        cudaFuncSetAttribute(k_rk3_tma<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_BYTES);
         attr_done = true;
     }
     return cudaGetLastError();
@@ -451,6 +492,7 @@ static StageDesc make_desc(const Solve &sv, int stage, int r, int chunk) {
     A.eps[1] = 1e-6f;                    // source indicator (dimensionless)
     A.eps[2] = (float)(1e-6 * g.dth * g.dth);
     A.eps[3] = (float)(1e-6 * (h / sv.c_ref) * (h / sv.c_ref));
+    A.polls = sv.wait_polls ? sv.wait_polls : DEFAULT_POLLS;
     A.tiles_x = (g.nx + tma::TX - 1) / tma::TX;
     A.tiles_z = (g.nz + tma::TZ - 1) / tma::TZ;
     A.chunk = chunk > g.nth ? g.nth : chunk;
@@ -465,13 +507,22 @@ static StageDesc make_desc(const Solve &sv, int stage, int r, int chunk) {
     return A;
 }
 
-static void launch_stage(int stage, const StageDesc *d, int nsolves, int total, unsigned *err, cudaStream_t s) {
+static void launch_stage(int stage, const StageDesc *d, int nsolves, int total, unsigned *err, cudaStream_t s,
+                         bool bounded) {
     int sms = sm_count() * tma::CTAS_PER_SM;
     int grid = total < sms ? total : sms;
     if (grid < 1) return;
-    if (stage == 1) k_rk3_tma<1><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);
-    if (stage == 2) k_rk3_tma<2><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);
-    if (stage == 3) k_rk3_tma<3><<<grid, tma::THREADS, tma::SMEM_BYTES, s>>>(d, nsolves, total, err);
+    const int T = tma::THREADS;
+    const size_t M = tma::SMEM_BYTES;
+    if (!bounded) {
+        if (stage == 1) k_rk3_tma<1, false><<<grid, T, M, s>>>(d, nsolves, total, err);
+        if (stage == 2) k_rk3_tma<2, false><<<grid, T, M, s>>>(d, nsolves, total, err);
+        if (stage == 3) k_rk3_tma<3, false><<<grid, T, M, s>>>(d, nsolves, total, err);
+    } else {
+        if (stage == 1) k_rk3_tma<1, true><<<grid, T, M, s>>>(d, nsolves, total, err);
+        if (stage == 2) k_rk3_tma<2, true><<<grid, T, M, s>>>(d, nsolves, total, err);
+        if (stage == 3) k_rk3_tma<3, true><<<grid, T, M, s>>>(d, nsolves, total, err);
+    }
 }
 
 int tma_chunk(const Solve &sv) { return sv.tma ? ((TmaMaps *)sv.tma)->chunk : 0; }
@@ -494,9 +545,10 @@ cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream
         if (ch > sv.g.nth && ci > 0) break;
         StageDesc h = make_desc(sv, 1, 0, ch);
         cudaMemcpyAsync(d_desc, &h, sizeof h, cudaMemcpyHostToDevice, s);
-        launch_stage(1, d_desc, 1, h.items, err, s);  // warm
+        bool bounded = sv.wait_polls != 0;
+        launch_stage(1, d_desc, 1, h.items, err, s, bounded);  // warm
         cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) launch_stage(1, d_desc, 1, h.items, err, s);
+        for (int rep = 0; rep < 3; ++rep) launch_stage(1, d_desc, 1, h.items, err, s, bounded);
         cudaEventRecord(e1, s);
         cudaError_t er = cudaEventSynchronize(e1);
         if (er != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return er; }
@@ -512,7 +564,9 @@ cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream
 
 // Advance several FP32 solves together: per stage one persistent launch over the work items of all
 // of them.  Whole 3-step rotations are captured once into a CUDA graph and replayed; the rest are
-// launched directly.  d_desc must hold 9 * n descriptors; cap is a non-legacy stream for capture.
+// launched directly.  After every step whose count (sv->steps, the steps before this call, plus the
+// steps taken in it) is a multiple of BRANCH_SAMPLE, the solve's continued spreading argument is
+// sampled.  d_desc must hold 9 * n descriptors; cap is a non-legacy stream for capture.
 cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
                          cudaStream_t cap) {
     if (n <= 0 || steps <= 0) return cudaSuccess;
@@ -532,27 +586,54 @@ cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsign
         }
     cudaError_t e = cudaMemcpyAsync(d_desc, h.data(), h.size() * sizeof(StageDesc), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
+    bool bounded = false;  // any solve with a caller-set wait bound (they share their context's)
+    for (int i = 0; i < n; ++i) bounded = bounded || sv[i]->wait_polls != 0;
     auto run_step = [&](int r, cudaStream_t st) {
         for (int stage = 1; stage <= 3; ++stage) {
             int slot = r * 3 + (stage - 1);
-            launch_stage(stage, d_desc + (size_t)slot * n, n, total[slot], err, st);
+            launch_stage(stage, d_desc + (size_t)slot * n, n, total[slot], err, st, bounded);
         }
     };
-    int rotations = steps / 3, rest = steps % 3;
-    if (rotations > 0) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return e;
-        for (int r = 0; r < 3; ++r) run_step(r, cap);
-        e = cudaStreamEndCapture(cap, &graph);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-        for (int i = 0; i < rotations && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, s);
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return e;
+    // step j of this call runs rotation phase j % 3; a rotation starting at a phase-0 step is one
+    // launch of the captured graph (captured at its first use)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto rotation = [&]() -> cudaError_t {
+        if (!exec) {
+            cudaError_t er = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (er != cudaSuccess) return er;
+            for (int r = 0; r < 3; ++r) run_step(r, cap);
+            er = cudaStreamEndCapture(cap, &graph);
+            if (er == cudaSuccess) er = cudaGraphInstantiate(&exec, graph, 0);
+            if (er != cudaSuccess) return er;
+        }
+        return cudaGraphLaunch(exec, s);
+    };
+    int j = 0;
+    while (j < steps && e == cudaSuccess) {
+        // steps to the next branch sample of any solve (or to the end of the call)
+        int seg = steps - j;
+        for (int i = 0; i < n; ++i) {
+            int to = BRANCH_SAMPLE - (int)((sv[i]->steps + j) % BRANCH_SAMPLE);
+            seg = to < seg ? to : seg;
+        }
+        for (int q = j; q < j + seg && e == cudaSuccess;) {
+            if (q % 3 == 0 && j + seg - q >= 3) {
+                e = rotation();
+                q += 3;
+            } else {
+                run_step(q % 3, s);
+                ++q;
+            }
+        }
+        j += seg;
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            if ((sv[i]->steps + j) % BRANCH_SAMPLE == 0)
+                e = launch_track_branch(*sv[i], sv[i]->state[(sv[i]->cur + j) % 3], false, s);
     }
-    for (int r = 0; r < rest; ++r) run_step(r, s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
     for (int i = 0; i < n; ++i) sv[i]->cur = (sv[i]->cur + steps) % 3;
     return cudaGetLastError();
 }

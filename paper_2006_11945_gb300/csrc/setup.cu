@@ -304,7 +304,9 @@ __global__ void k_frozen(Grid2D g, const double *__restrict__ gsd, double xs, do
     double dz = __dadd_rn(__dadd_rn(g.oz, __dmul_rn((double)iz, g.hz)), -zs);
     double r2 = __dadd_rn(__dmul_rn(dz, dz), __dmul_rn(dx, dx));
     double dot = __dadd_rn(__dmul_rn(dx, gx), __dmul_rn(dz, gz));
-    bool f = r2 <= __dmul_rn(r0, r0) || (r2 <= __dmul_rn(R, R) && dot < 0.0);
+    // a cell on the closest-approach line (d . g_s at rounding level) belongs to the leaving half
+    bool approach = dot < 0.0 && __dmul_rn(dot, dot) > __dmul_rn(1e-24, r2);
+    bool f = r2 <= __dmul_rn(r0, r0) || (r2 <= __dmul_rn(R, R) && approach);
     frozen[cidx(g, k, iz, ix)] = f ? 1 : 0;
 }
 

@@ -15,6 +15,9 @@
 //                  rays), blended by b_x^2/|grad b|^2 + b_z^2/|grad b|^2 = 1                (Eq. 34)
 //  k_arrivals      per receiver: sign changes of b along theta -> traveltime and geometrical
 //                  amplitude of every arrival, late arrivals included
+//  k_track_branch  per cell, every BRANCH_SAMPLE steps of the evolution: the argument of the
+//                  complex spreading continued through pseudo-time, which fixes the sheet of
+//                  Eq. 26's square root past caustics (KMAH index)
 #include "christoffel.cuh"
 
 namespace egb {
@@ -34,6 +37,8 @@ struct SupArgs {
     int n_omega;
     const double *omega_dev;
     float w0;
+    float iw0;              // 1 / w0: scale of the take-off family in the reference spreading
+    const float *alpha;     // [cells] continued argument of the reference spreading
     const uint8_t *frozen;  // [cells] frozen source manifold
     float C1, C2, C3;     // 2 pi split for the range reduction
     unsigned *err;
@@ -116,6 +121,97 @@ __device__ CellData load_cell(const SupArgs &A, int k, int iz, int ix) {
     return d;
 }
 
+// Phase-space perturbations that keep the ray direction e = (Vx, Vz, thetadot) and change the
+// labels (b, vartheta) by (1, 0) and (0, 1): db = (k2 x e) / D, dT = (e x k1) / D with k1 = grad b,
+// k2 = grad vartheta and D = e . (k1 x k2) (the dynamic ray tracing from the level sets).  D is the
+// orientation of the label coordinates (b, vartheta, tau), negative on the straight-ray data and,
+// the label map being one-to-one on the source tube, negative throughout: a positive discrete D
+// (under-resolved labels) is taken as -|D|, which keeps J's orientation and its argument
+// continuous where the discrete D passes through zero.
+__device__ __forceinline__ void ray_families(const float e[3], const float k1[3], const float k2[3],
+                                             float db[3], float dT[3]) {
+    float x12[3] = {k1[1] * k2[2] - k1[2] * k2[1], k1[2] * k2[0] - k1[0] * k2[2], k1[0] * k2[1] - k1[1] * k2[0]};
+    float D = e[0] * x12[0] + e[1] * x12[1] + e[2] * x12[2];
+    float iD = -1.f / fabsf(D);
+    db[0] = (k2[1] * e[2] - k2[2] * e[1]) * iD;
+    db[1] = (k2[2] * e[0] - k2[0] * e[2]) * iD;
+    db[2] = (k2[0] * e[1] - k2[1] * e[0]) * iD;
+    dT[0] = (e[1] * k1[2] - e[2] * k1[1]) * iD;
+    dT[1] = (e[2] * k1[0] - e[0] * k1[2]) * iD;
+    dT[2] = (e[0] * k1[1] - e[1] * k1[0]) * iD;
+}
+
+// Principal argument of the reference spreading J_ref = J_b + i J_T / w0 (J = dx x V of the offset
+// family db and of the take-off family dT); false where the level-set Jacobian is singular.
+__device__ __forceinline__ bool ref_arg(const float db[3], const float dT[3], float Vx, float Vz,
+                                        float iw0, float &a) {
+    float Jb = db[0] * Vz - db[1] * Vx, JT = dT[0] * Vz - dT[1] * Vx;
+    if (!(isfinite(Jb) && isfinite(JT))) return false;
+    a = atan2f(JT * iw0, Jb);
+    return true;
+}
+__device__ __forceinline__ bool cell_ref_arg(float bx, float bz, float bt, float tx, float tz, float tt,
+                                             float Vx, float Vz, float td, float iw0, float &a) {
+    float e[3] = {Vx, Vz, td}, k1[3] = {bx, bz, bt}, k2[3] = {tx, tz, tt}, db[3], dT[3];
+    ray_families(e, k1, k2, db, dT);
+    return ref_arg(db, dT, Vx, Vz, iw0, a);
+}
+// The value a + 2 pi k (k integer) nearest to alpha.
+__device__ __forceinline__ float lift_branch(float alpha, float a) {
+    const float two_pi = 6.28318530717958647692f;
+    return a + two_pi * rintf((alpha - a) * 0.159154943091895335769f);
+}
+
+// One sample of the continued argument on every cell of the padded state `st` (init: the initial
+// data, which has no caustic, gives the principal argument; otherwise the stored value is lifted to
+// the current principal argument, and kept where the level-set Jacobian is singular).  The complex
+// spreading of the beam family never vanishes and the labels change continuously in pseudo-time,
+// so sampled often enough this follows its argument from the straight-ray initial data to the
+// steady state, which carries it onto the argument continued along the ray.
+// One thread per (x, z) column and chunk of TRACK_CHUNK angle planes marches through them with the
+// column's b and vartheta of planes k-1, k, k+1 in registers, so a value is read from memory about
+// once; the x and z neighbours come through L1/L2 (neighbouring blocks advance nearly in step).
+constexpr int TRACK_CHUNK = 32;
+__global__ void k_track_branch(Grid2D g, const float *__restrict__ st, const float *__restrict__ vel,
+                               float iw0, float *__restrict__ alpha, int init) {
+    int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    int iz = blockIdx.y;
+    int k0 = blockIdx.z * TRACK_CHUNK, k1 = min(k0 + TRACK_CHUNK, g.nth);
+    if (ix >= g.nx) return;
+    float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
+    const float *B = st, *Th = st + 2 * g.field;
+    const int64_t p0 = pidx(g, 0, iz, ix), cells = (int64_t)g.nth * g.nx * g.nz;
+    const int64_t o0 = cidx(g, 0, iz, ix), oplane = (int64_t)g.nx * g.nz;
+    int kl = k0 == 0 ? g.nth - 1 : k0 - 1;
+    float bm = B[p0 + kl * g.plane], tm = Th[p0 + kl * g.plane];
+    float bc = B[p0 + (int64_t)k0 * g.plane], tc = Th[p0 + (int64_t)k0 * g.plane];
+    for (int k = k0; k < k1; ++k) {
+        int kn = k + 1 == g.nth ? 0 : k + 1;
+        int64_t p = p0 + (int64_t)k * g.plane;
+        float bn = B[p0 + (int64_t)kn * g.plane], tn = Th[p0 + (int64_t)kn * g.plane];
+        float bx = grad_line(B, p, ix, g.nx, 1, ihx);
+        float bz = grad_line(B, p, iz, g.nz, g.pitch, ihz);
+        float bt = (bn - bm) * 0.5f * idth;
+        float tx = grad_line_angle(Th, p, ix, g.nx, 1, ihx);
+        float tz = grad_line_angle(Th, p, iz, g.nz, g.pitch, ihz);
+        float tt = wrap_angle(tn - tm) * 0.5f * idth;
+        int64_t o = o0 + (int64_t)k * oplane;
+        float a = 0.f;
+        bool ok = cell_ref_arg(bx, bz, bt, tx, tz, tt, vel[o], vel[cells + o], vel[2 * cells + o], iw0, a);
+        if (init) alpha[o] = ok ? a : 0.f;
+        else if (ok) alpha[o] = lift_branch(alpha[o], a);
+        bm = bc; tm = tc;
+        bc = bn; tc = tn;
+    }
+}
+
+cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cudaStream_t s) {
+    const Grid2D &g = sv.g;
+    dim3 grid((g.nx + 127) / 128, g.nz, (g.nth + TRACK_CHUNK - 1) / TRACK_CHUNK);
+    k_track_branch<<<grid, 128, 0, s>>>(g, st, sv.vel, (float)(1.0 / sv.w0), sv.alpha, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
 struct cf { float re, im; };
 __device__ __forceinline__ cf cmul(cf a, cf b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __device__ __forceinline__ cf cdiv(cf a, cf b) {
@@ -186,14 +282,20 @@ __global__ void k_centres(SupArgs A) {
         float tau_hi = c0.tau_hi;
         float tau_lo = c0.tau_lo + t * ((c1.tau_hi - c0.tau_hi) + (c1.tau_lo - c0.tau_lo));
         // dynamic ray tracing from the label gradients
-        float e[3] = {Vx, Vz, td}, k1[3] = {bx, bz, bt}, k2[3] = {tx, tz, tt};
-        float x12[3] = {k1[1] * k2[2] - k1[2] * k2[1], k1[2] * k2[0] - k1[0] * k2[2], k1[0] * k2[1] - k1[1] * k2[0]};
-        float D = e[0] * x12[0] + e[1] * x12[1] + e[2] * x12[2];
-        float iD = 1.f / D;
-        float db[3] = {(k2[1] * e[2] - k2[2] * e[1]) * iD, (k2[2] * e[0] - k2[0] * e[2]) * iD,
-                       (k2[0] * e[1] - k2[1] * e[0]) * iD};
-        float dT[3] = {(e[1] * k1[2] - e[2] * k1[1]) * iD, (e[2] * k1[0] - e[0] * k1[2]) * iD,
-                       (e[0] * k1[1] - e[1] * k1[0]) * iD};
+        float e[3] = {Vx, Vz, td}, k1[3] = {bx, bz, bt}, k2[3] = {tx, tz, tt}, db[3], dT[3];
+        ray_families(e, k1, k2, db, dT);
+        // sheet of the square root: the continued argument, sampled once more on both cells and
+        // interpolated, against the principal argument of the reference spreading at the centre
+        float al0 = A.alpha[o0], al1 = A.alpha[o1], a0, a1, ac;
+        if (cell_ref_arg(c0.bx, c0.bz, c0.bt, c0.tx, c0.tz, c0.tt, c0.Vx, c0.Vz, c0.td, A.iw0, a0))
+            al0 = lift_branch(al0, a0);
+        if (cell_ref_arg(c1.bx, c1.bz, c1.bt, c1.tx, c1.tz, c1.tt, c1.Vx, c1.Vz, c1.td, A.iw0, a1))
+            al1 = lift_branch(al1, a1);
+        float sigma = 1.f;
+        if (ref_arg(db, dT, Vx, Vz, A.iw0, ac)) {
+            float kk = rintf((L(al0, al1) - ac) * 0.159154943091895335769f);
+            sigma = (((int)kk) & 1) ? -1.f : 1.f;
+        }
         float ss, cs;
         sincosf(thc, &ss, &cs);
         SrcVel sv = source_velocity(as, ss, cs);
@@ -229,10 +331,8 @@ __global__ void k_centres(SupArgs A) {
             cf M;
             if (ROW) M = cdiv(cf{dpx.re * Vz - pdx * dz.re, dpx.im * Vz - pdx * dz.im}, J);
             else M = cdiv(cf{-dpz.re * Vx + pdz * dx.re, -dpz.im * Vx + pdz * dx.im}, J);
-            // KMAH index 1: at the first caustic J leaves the upper half plane through the negative
-            // real axis, where the principal root jumps; sigma = -1 once arg J < -1e-3 (near the
-            // source J is close to the positive real axis and sigma stays +1)
-            float sigma = atan2f(J.im, J.re) < -1e-3f ? -1.f : 1.f;
+            // square root continued along the ray: J = J_b + kappa J_T has the sign of Im J_ref, so
+            // the sheet found for J_ref is this frequency's too
             cf amp = csqrt_pr(cdiv(cf{rho_s * sv.Vn / rho, 0.f}, J));
             // coef = i * wreal * sigma * amp
             cf coef = {-wreal * sigma * amp.im, wreal * sigma * amp.re};
@@ -256,49 +356,56 @@ __global__ void k_centres(SupArgs A) {
     (ROW ? A.rcnt : A.ccnt)[(int64_t)k * nl + line] = cnt;
 }
 
+// One beam's term at a receiver offset d along its grid line (d in m), accumulated into (re, im).
+__device__ __forceinline__ void beam_term(float d, float om, float p, float4 q, float &re, float &im) {
+    float ph = om * (p * d + 0.5f * q.z * d * d);
+    float dec = -0.5f * om * q.w * d * d;
+    if (dec < -60.f) return;
+    float mag = __expf(dec);
+    float sp, cp;
+    sincosf(ph, &sp, &cp);
+    re += mag * (q.x * cp - q.y * sp);
+    im += mag * (q.x * sp + q.y * cp);
+}
+
+// Eq. 34 per receiver: the sum over angles of the beams centred on its row and its column.  The
+// angles of one receiver are split over SUM_LANES lanes of a warp (lane t takes theta_k with
+// k = t mod SUM_LANES), whose partial sums are reduced with butterfly shuffles; a warp serves
+// 32 / SUM_LANES neighbouring receivers of one row, so the lanes of one angle read the same beam
+// data (the row's beams are shared by all its receivers).
+constexpr int SUM_LANES = 8;
 __global__ void k_sum(SupArgs A, float2 *u) {
     const Grid2D &g = A.g;
-    int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    int iz = blockIdx.y;
-    if (ix >= g.nx) return;
-    float xr = (float)((double)ix * g.hx), zr = (float)((double)iz * g.hz);
+    const int lane = threadIdx.x & 31, t = lane % SUM_LANES;
+    const int ix = blockIdx.x * (blockDim.x / SUM_LANES) + threadIdx.x / SUM_LANES;
+    const int iz = blockIdx.y;
+    const bool rx = ix < g.nx;  // lanes past the row's end still take part in the shuffles
+    const int ixc = rx ? ix : g.nx - 1;
+    float xr = (float)((double)ixc * g.hx), zr = (float)((double)iz * g.hz);
     int64_t rows_total = (int64_t)g.nth * g.nz * KC, cols_total = (int64_t)g.nth * g.nx * KC;
     for (int w = 0; w < A.n_omega; ++w) {
         float om = (float)A.omega_dev[w];
         float are = 0.f, aim = 0.f;
-        for (int k = 0; k < g.nth; ++k) {
+        for (int k = t; k < g.nth; k += SUM_LANES) {
             int64_t rl = (int64_t)k * g.nz + iz;
             int nr = A.rcnt[rl];
             for (int j = 0; j < nr; ++j) {
                 int64_t s = rl * KC + j;
-                float d = xr - A.rpos[s];
-                float4 q = A.rdat[(int64_t)w * rows_total + s];
-                float ph = om * (A.rp[s] * d + 0.5f * q.z * d * d);
-                float dec = -0.5f * om * q.w * d * d;
-                if (dec < -60.f) continue;
-                float mag = __expf(dec);
-                float sp, cp;
-                sincosf(ph, &sp, &cp);
-                are += mag * (q.x * cp - q.y * sp);
-                aim += mag * (q.x * sp + q.y * cp);
+                beam_term(xr - A.rpos[s], om, A.rp[s], A.rdat[(int64_t)w * rows_total + s], are, aim);
             }
-            int64_t cl = (int64_t)k * g.nx + ix;
+            int64_t cl = (int64_t)k * g.nx + ixc;
             int nc = A.ccnt[cl];
             for (int j = 0; j < nc; ++j) {
                 int64_t s = cl * KC + j;
-                float d = zr - A.cpos[s];
-                float4 q = A.cdat[(int64_t)w * cols_total + s];
-                float ph = om * (A.cp[s] * d + 0.5f * q.z * d * d);
-                float dec = -0.5f * om * q.w * d * d;
-                if (dec < -60.f) continue;
-                float mag = __expf(dec);
-                float sp, cp;
-                sincosf(ph, &sp, &cp);
-                are += mag * (q.x * cp - q.y * sp);
-                aim += mag * (q.x * sp + q.y * cp);
+                beam_term(zr - A.cpos[s], om, A.cp[s], A.cdat[(int64_t)w * cols_total + s], are, aim);
             }
         }
-        u[((int64_t)w * g.nz + iz) * g.nx + ix] = make_float2(are, aim);
+#pragma unroll
+        for (int m = SUM_LANES / 2; m > 0; m >>= 1) {
+            are += __shfl_xor_sync(0xffffffffu, are, m);
+            aim += __shfl_xor_sync(0xffffffffu, aim, m);
+        }
+        if (rx && t == 0) u[((int64_t)w * g.nz + iz) * g.nx + ix] = make_float2(are, aim);
     }
 }
 
@@ -408,6 +515,8 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
     A.vel = sv.vel;
     A.rho = sv.m->rho;
     A.src = sv.src;
+    A.alpha = sv.alpha;
+    A.iw0 = (float)(1.0 / sv.w0);
     A.B = (float *)take(cells * 4);
     A.VSN = (float *)take(cells * 4);
     A.FL = (uint8_t *)take(cells);
@@ -433,7 +542,7 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
     if (u_dev) {
         k_centres<true><<<dim3((g.nz + 63) / 64, g.nth), 64, 0, s>>>(A);
         k_centres<false><<<dim3((g.nx + 63) / 64, g.nth), 64, 0, s>>>(A);
-        k_sum<<<dim3((g.nx + 127) / 128, g.nz), 128, 0, s>>>(A, u_dev);
+        k_sum<<<dim3((g.nx + 256 / SUM_LANES - 1) / (256 / SUM_LANES), g.nz), 256, 0, s>>>(A, u_dev);
     }
     if (count_dev || T_dev || A_dev)
         k_arrivals<<<dim3((g.nx + 63) / 64, g.nz), 64, 0, s>>>(A, count_dev, T_dev, A_dev, kmax);

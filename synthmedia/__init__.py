@@ -105,9 +105,18 @@ def rotate_voigt_about_y(C, tilt):
     R[..., 1, 1] = 1.0
     R[..., 2, 0] = -st
     R[..., 2, 2] = ct
-    c = _voigt_to_tensor(C)
-    c = np.einsum('...ip,...jq,...kr,...ls,...pqrs->...ijkl', R, R, R, R, c, optimize=True)
-    return _tensor_to_voigt(c)
+    # Bond's 6x6 form of c'_ijkl = R_ip R_jq R_kr R_ls c_pqrs: C' = M C M^T with the stress
+    # transformation M_IJ = R_ik R_jl + R_il R_jk (k != l) or R_ik R_jk (k = l), I ~ (i, j), J ~ (k, l)
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    M = np.empty(tilt.shape + (6, 6))
+    for I, (i, j) in enumerate(pairs):
+        for J, (k, l) in enumerate(pairs):
+            M[..., I, J] = R[..., i, k] * R[..., j, l]
+            if k != l:
+                M[..., I, J] += R[..., i, l] * R[..., j, k]
+    C = np.broadcast_to(np.asarray(C, np.float64), tilt.shape + (6, 6))
+    MC = sum(M[..., :, j, None] * C[..., None, j, :] for j in range(6))
+    return sum(MC[..., :, k, None] * M[..., None, :, k] for k in range(6))
 
 
 def voigt_to_c21(C):
@@ -199,6 +208,26 @@ def isotropic_homogeneous(n=64, h=10.0, n_theta=64, steps=150, vp=3000.0, vs=170
         xs = ((n // 2) * h, (n // 2) * h)
     return Problem2D('isotropic_homogeneous', n, n, h, h, c21, r, xs, n_theta, list(freqs),
                      beam_width, steps, cfl, meta=dict(vp=vp, vs=vs, rho=rho))
+
+
+def v_channel(nx=128, nz=64, h=10.0, n_theta=256, gradient=0.002, smoothing=30.0, vp0=3000.0,
+              freqs=(50.0, 100.0, 200.0), beam_width=40.0, steps=200, cfl=0.5, x_source=100.0):
+    """Isotropic low-velocity channel: vp = vp0 (1 + g (sqrt((z - z_c)^2 + a^2) - a)) about the
+    middle row z_c (a V-shaped profile rounded over a), vs = vp / 1.8, rho 2300; the source on the
+    channel axis at x_source.  Rays within the trapping angle oscillate about the axis and touch a
+    caustic every half period, so arrivals late in the channel have passed two caustics and more."""
+    x = np.arange(nx) * h
+    z = np.arange(nz) * h
+    Z, _ = np.meshgrid(z, x, indexing='ij')
+    zc = z[nz // 2]
+    vp = vp0 * (1.0 + gradient * (np.sqrt((Z - zc) ** 2 + smoothing ** 2) - smoothing))
+    vs, rho = vp / 1.8, 2300.0
+    mu = rho * vs ** 2
+    C = isotropic_voigt(rho * vp ** 2 - 2 * mu, mu)
+    c21, r = _pack(C, np.full((nz, nx), rho))
+    return Problem2D('v_channel', nx, nz, h, h, c21, r, (float(x_source), float(zc)), n_theta,
+                     list(freqs), beam_width, steps, cfl,
+                     meta=dict(vp0=vp0, gradient=gradient, smoothing=smoothing))
 
 
 def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 40.0),

@@ -43,3 +43,24 @@ def test_sources_sharing_a_medium_equal_separate_solves():
         assert info['dt'] == alone_info['dt']
     cells = infos[0]['cells']
     assert infos[0]['device_bytes'] - infos[1]['device_bytes'] == 24 * cells
+
+
+def test_sources_sharing_a_medium_match_the_oracle():
+    """Both solves on the shared medium (the second reusing the first's velocities) against the FP64
+    oracle run for each source on its own, at the parity bar."""
+    import paper_2006_11945_gb300 as egb
+    from tests.gpu_common import compare_outputs, run_oracle
+    p, q = _problems()
+    with egb.Context(0) as ctx:
+        m = ctx.medium_2d(p)
+        ids = [ctx.source_2d(m, x) for x in (p, q)]
+        res = []
+        for s, x in zip(ids, (p, q)):
+            ctx.evolve(s, x.steps, x.cfl)
+            res.append(ctx.superpose(s, len(x.freqs), x.nz, x.nx, 8))
+        egb.egb_sync(ctx.h)
+    for x, r in zip((p, q), res):
+        mt = compare_outputs(r, run_oracle(x))
+        print(x.xs, mt)
+        assert mt['u_rel_l2'] < 2e-3 and mt['count_mismatch'] == 0, mt
+        assert mt['T_rel_max'] < 1e-5 and mt['A_rel_max'] < 1e-3, mt
