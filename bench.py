@@ -46,8 +46,8 @@ ALGO_BYTES_PER_CELL_UPDATE = 52.0
 # (stage 1: 917 MB, stages 2 and 3: 1285 and 1284 MB per 16.8 M cells), with the SHA-256 of the
 # kernel's device source it was taken on; traffic grows with the cells a launch processes, so the
 # figure is scaled to the timed workload.  Reported as null once the device source differs.
-STENCIL_TRAFFIC = {'bytes_per_cell_launch': (54.6 + 76.6 + 76.5) / 3.0,
-                   'device_source_sha256': '234b76e65aa44ff578a3fe77136950a77d740b6ec3aa9e4af51321c0f1707ba1'}
+STENCIL_TRAFFIC = {'bytes_per_cell_launch': (54.75 + 78.44 + 78.58) / 3.0,
+                   'device_source_sha256': '43f3a363c8d7ceedc11ad8b8a6f391e386d072b408408a702fb643433420d06e'}
 
 
 def stencil_traffic_per_launch(cells):
@@ -57,6 +57,17 @@ def stencil_traffic_per_launch(cells):
     if hashlib.sha256(src[a:b].encode()).hexdigest() != STENCIL_TRAFFIC['device_source_sha256']:
         return None
     return STENCIL_TRAFFIC['bytes_per_cell_launch'] * cells
+
+
+# Instruction issue of k_rk3_tma per cell and stage launch (ncu, thread-level instructions of the
+# stage-2 launch on the 256^2 x 256 TTI case: 329.5, of which FP32 182.3 and integer 66.0), and
+# GB300's issue ceiling: 4 schedulers per SM issue one warp instruction (32 thread instructions)
+# per cycle.
+STENCIL_THREAD_INST_PER_CELL_STAGE = 329.5
+
+
+def issue_ceiling_thread_inst_per_s(sm_mhz):
+    return 152 * 4 * 32 * sm_mhz * 1e6
 
 
 # 3-D: the state (six FP32 labels b, n0, the indicator q and the double-float tau: 36 B) read and
@@ -282,6 +293,14 @@ def run_egb(args):
         'gpu_launches': launches * args.steps,
         'clocks': clk.summary(),
     }
+    # the stencil against its instruction-issue ceiling (at the median SM clock of the timed region)
+    mhz = line['clocks'].get('sm_mhz') or 2070.0
+    inst_rate = STENCIL_THREAD_INST_PER_CELL_STAGE * cells / (launch_ms / 1e3)
+    line['issue_ceiling'] = {'kernel': 'k_rk3_tma', 'thread_inst_per_cell_stage': STENCIL_THREAD_INST_PER_CELL_STAGE,
+                             'achieved': inst_rate, 'peak': issue_ceiling_thread_inst_per_s(mhz),
+                             'unit': 'thread instructions/s', 'frac': inst_rate / issue_ceiling_thread_inst_per_s(mhz),
+                             'hbm_frac_at_ceiling': ALGO_BYTES_PER_CELL_UPDATE * issue_ceiling_thread_inst_per_s(mhz)
+                             / (3 * STENCIL_THREAD_INST_PER_CELL_STAGE) / (peak * 1e9)}
     if not args.no_fp64_form:
         line['fp64_form'] = fp64_form(p, args.fp64_steps, local)
         line['fp64_form']['speedup'] = line['value'] / ws / line['fp64_form']['value']
@@ -295,6 +314,7 @@ def run_egb(args):
             'tri96': measure_3d(p3, p3.steps, 1, 1, warmup_steps=3),
             'batch': measure_batch_waves(synthmedia.batched_instances(count=args.batch_count),
                                          args.evolve_steps or 10, 1, 1),
+            'reductions': measure_receiver(p),
             'serve': measure_serve(args.serve_seconds, 1.0, args.serve_chunk,
                                    args.serve_wall if args.serve_wall is not None else 60.0,
                                    args.serve_chunk_work, args.serve_max_chunk_work),
@@ -312,6 +332,47 @@ def run_egb3d(args):
     torch.cuda.set_device(0)
     p = workload(args.workload)
     print(json.dumps(measure_3d(p, args.evolve_steps or 20, args.steps, args.warmup)))
+
+
+def measure_receiver(p, K=5, W=2):
+    """The two reductions of one evolved state, each timed on its own (CUDA events on the context's
+    stream, W untimed calls first): the source-side superposition with arrivals (egb_superpose) and
+    the receiver-side reciprocal sum (egb_superpose_receiver), both into device buffers.  Their unit
+    is a beam-point sum: one phase cell at one frequency."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    stream = torch.cuda.Stream()
+    no, kmax = len(p.freqs), 8
+    u_d = torch.empty((no, p.nz, p.nx, 2), dtype=torch.float32, device='cuda')
+    cnt_d = torch.empty((p.nz, p.nx), dtype=torch.uint8, device='cuda')
+    T_d = torch.empty((p.nz, p.nx, kmax), dtype=torch.float64, device='cuda')
+    A_d = torch.empty((p.nz, p.nx, kmax), dtype=torch.float32, device='cuda')
+    out = {}
+    with egb.Context(0, stream.cuda_stream) as ctx:
+        m = ctx.medium_2d(p)
+        s = ctx.source_2d(m, p)
+        ctx.evolve(s, p.steps, p.cfl)
+        calls = {'source_side': lambda: egb.egb_superpose(ctx.h, s, u_d, cnt_d, T_d, A_d, kmax),
+                 'receiver_side': lambda: egb.egb_superpose_receiver(ctx.h, s, u_d)}
+        cells = p.nx * p.nz * p.n_theta
+        for name, fn in calls.items():
+            for _ in range(W):
+                fn()
+            egb.egb_sync(ctx.h)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                t0.record(stream)
+            for _ in range(K):
+                fn()
+            with torch.cuda.stream(stream):
+                t1.record(stream)
+            egb.egb_sync(ctx.h)
+            ms = t0.elapsed_time(t1) / K
+            out[name] = {'ms': ms, 'beam_point_sums_per_s': cells * no / (ms / 1e3)}
+    out['workload'] = (f'{p.name} {p.nx}x{p.nz} x {p.n_theta} angles after {p.steps} steps, '
+                       f'{no} frequencies; state resident, no flush (the reductions read it once)')
+    out['calls'] = K
+    return out
 
 
 def measure_3d(p, steps_evolve, K, W, warmup_steps=None):
@@ -875,6 +936,8 @@ def main():
     ap.add_argument('--serve-max-chunk-work', type=float, default=2e10,
                     help='bound on the work of one chunk: admission shortest-work-first under it')
     ap.add_argument('--no-sub', action='store_true', help='skip the 3-D, batch and serving sub-records')
+    ap.add_argument('--reductions', action='store_true',
+                    help='time only the source-side and receiver-side reductions of one evolved state')
     ap.add_argument('--evolve-steps', type=int, default=None)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--cpu-seconds', type=float, default=20.0)
@@ -885,6 +948,14 @@ def main():
         run_reference(args)
     elif args.workload == 'serve':
         run_serve(args)
+    elif args.reductions:
+        import dataclasses
+        import torch
+        torch.cuda.set_device(0)
+        p = workload(args.workload)
+        if args.evolve_steps is not None:
+            p = dataclasses.replace(p, steps=args.evolve_steps)
+        print(json.dumps(measure_receiver(p, K=args.steps, W=args.warmup)))
     elif args.workload in ('tri96', 'tri48'):
         run_egb3d(args)
     elif args.workload == 'batch':

@@ -106,6 +106,9 @@ egb_status egb_medium(egb_ctx *ctx, int dim, const int n[3], const double h[3],
  *               R_Sigma = max(4 r0, min(Lx, Lz)/8) of x_s whose ray still approaches the source are
  *               frozen too (the closest-approach manifold that replaces Eq. 20's initial plane;
  *               3-D: R_Sigma = max(4 r0, min(Lx, Ly, Lz)/8), r0 default 2*max(hx, hy, hz))
+ *   R_sigma     that disc's radius (m) when > 0 (at least r0); <= 0 selects the default above.  Rays
+ *               passing within R_Sigma of x_s carry source labels (the source-ray tube, twice
+ *               R_Sigma wide); the receiver-side reduction needs it at least twice the beam width
  * The characteristic velocities depend on the medium and the phase angles only: in 2-D (FP32
  * precision) the first solve on a medium computes them for its angle count and later solves on the
  * same medium with the same count reuse them (the medium owns them until it is released).
@@ -116,7 +119,7 @@ egb_status egb_medium(egb_ctx *ctx, int dim, const int n[3], const double h[3],
  * bound).  Errors: EGB_E_INVALID, EGB_E_NOMEM, EGB_E_NOT_PD (medium failed validation), EGB_E_CUDA. */
 egb_status egb_source(egb_ctx *ctx, egb_medium_id medium, const double xs[3], int n_omega,
                       const double *omega, double beam_width, const int n_ang[2], double r0,
-                      egb_solve_id *out);
+                      double R_sigma, egb_solve_id *out);
 
 /* Advance the level sets `steps` TVD-RK3 steps (HJ-WENO3 in x, z, theta; 3-D: x, y, z, theta, phi)
  * at Courant number cfl (0 < cfl <= 1); dt = cfl / max(|Vx|/hx + |Vz|/hz + |dtheta/dt|/dtheta)
@@ -147,6 +150,22 @@ egb_status egb_evolve_batch(egb_ctx *ctx, int n, const egb_solve_id *solves, con
  * EGB_E_ARRIVAL_OVERFLOW.  Errors: EGB_E_INVALID, EGB_E_CUDA. */
 egb_status egb_superpose(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t *count, double *T,
                          float *A, int kmax);
+
+/* The same Green's function as egb_superpose, summed from the receiver side (Eq. 34 read through
+ * reciprocity: the field at x0 of the source x_s is that at x_s of a source at x0).  For every
+ * receiver node x0 and every phase angle whose cell carries source labels (q > 1/2, not frozen),
+ * a Gaussian beam is launched back along the ray through (x0, theta): the level-set Jacobian at x0
+ * is the ray propagator to the ray's closest approach C to x_s (Sec. 4, the dynamic ray tracing of
+ * Eqs. 21-24 read from the labels), which gives the beam's width and curvature there (Eq. 25), its
+ * amplitude (Eq. 26) and its phase at x_s, tau + M b^2 / 2 (b the ray's offset from x_s at C).
+ * The sum over theta at x0, weighted as the source side (calibrated to (i/4) H0^(1) in a
+ * homogeneous isotropic medium), is rescaled by rho_s c_s^2 / (rho0 c0^2) to egb_superpose's
+ * normalisation.  Valid for arrivals without a caustic (KMAH index 0; principal square root); the
+ * beams reach x_s about as wide as w(r) = w0 sqrt(1 + (2 r / (k w0^2))^2), so the source-ray tube
+ * (egb_source's R_sigma) should be at least 2 w(r) for the farthest receiver.
+ *   u_out  complex64 [n_omega][nz][nx], host or device
+ * Errors: EGB_E_INVALID (3-D solve, unknown id, NULL u_out, no frequencies), EGB_E_NOMEM, EGB_E_CUDA. */
+egb_status egb_superpose_receiver(egb_ctx *ctx, egb_solve_id solve, void *u_out);
 
 /* Size of the fixed device scratch used by egb_superpose_noalloc (32 MiB). */
 #define EGB_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -148,7 +148,10 @@ def velocity_field_pooled(problem, processes=8):
 
 
 def source_disc_radius(problem, r0):
-    """R_Sigma = max(4 r0, min(Lx, Lz) / 8): radius of the closest-approach manifold's disc."""
+    """R_Sigma, the radius of the closest-approach manifold's disc: the problem's own value when it
+    sets one, else max(4 r0, min(Lx, Lz) / 8)."""
+    if getattr(problem, 'R_sigma', None):
+        return float(problem.R_sigma)
     Lx = (problem.nx - 1) * problem.hx
     Lz = (problem.nz - 1) * problem.hz
     return max(4.0 * r0, min(Lx, Lz) / 8.0)

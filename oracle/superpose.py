@@ -300,6 +300,74 @@ def green(S, lab, omegas, beam_width):
     return np.stack(out)
 
 
+def green_receiver(S, lab, omegas, beam_width):
+    """u(omega, z, x) complex128 by the receiver-side (reciprocal) reduction of the same labels.
+
+    Eq. 34 read from the receiver: by reciprocity the Green's function at x0 of the source x_s is
+    that at x_s of a source at x0, and it is summed from Gaussian beams launched at x0 along every
+    ray through x0 that carries source labels (q > 1/2, not frozen), evaluated at x_s.  The ray
+    through the cell (x0, theta) passes closest to x_s at C, at signed offset b, with phase angle
+    vartheta, tau after C.  A beam launched back along it with the perturbation
+    (dx_perp, dtheta) = (1, kappa0), kappa0 = -2 i |V0| / (omega w0^2) (the source side's initial
+    data mirrored for the reversed direction), reaches C with the offset and angle changes
+        db = b_perp + kappa0 b_theta,   dvartheta = vartheta_perp + kappa0 vartheta_theta
+    (the label Jacobian at x0 is the ray propagator to C; perp is along the unit normal
+    (g_z, -g_x) of the group direction g, the direction in which b grows).  Its Hessian there is
+    M = -(dp/dvartheta . (g_z, -g_x)) dvartheta / db (slowness of the source medium at vartheta; the
+    minus for the reversed ray), and its phase at x_s is tau + M b^2 / 2: tau already holds the
+    plane-wave part p_C . (x_C - x_s) of the offset.  Im M is taken from the beam's Wronskian
+    instead of the label Jacobian: the ray propagator is symplectic, so Im(conj(Q) P) keeps its
+    initial value and Im M = 2 |V0| (dp/dtheta . (g_z, -g_x))_x0 / (omega w0^2 |db|^2) exactly; the
+    label Jacobian satisfies this only up to its discretisation error, which near the edge of the
+    source-ray tube (labels bending onto boundary data) can leave Im M near zero at a small |db|, a
+    large undamped term whose phase then hangs on the last digit of the labels.  With the elastic
+    transport the amplitude there is sqrt(rho0 |V0| / (rho_s |V_s(vartheta)| db)) (principal root:
+    rays with no caustic, KMAH index 0), the weight per dtheta is i c0^2 / (4 pi v0(theta)^2) (c0 the phase velocity along +z at x0;
+    the same calibration as the source side, which gives (i/4) H0^(1)(kr) in a homogeneous isotropic
+    medium), and the sum, rho0 c0^2 times the Green's function, is rescaled by
+    rho_s c_s^2 / (rho0 c0^2) to the source side's normalisation.
+    """
+    b, q, Th, tau = lab['b'], lab['q'], lab['Th'], lab['tau']
+    G = _label_gradients(S, b, Th)
+    flag = (q > 0.5) & ~S.frozen
+    Vx, Vz, v0 = S.vel['Vx'], S.vel['Vz'], S.vel['v']
+    V0 = np.hypot(Vx, Vz)
+    gx, gz = Vx / V0, Vz / V0
+    b_perp = G['bx'] * gz - G['bz'] * gx
+    t_perp = G['Tx'] * gz - G['Tz'] * gx
+    # source medium at the closest approach: slowness derivative along vartheta, |V_s|
+    vs, Vs, Vsn, gs = _ch.source_quantities(S.a_s, Th)
+    n = np.stack([np.sin(Th), np.cos(Th)], -1)
+    n_t = np.stack([np.cos(Th), -np.sin(Th)], -1)
+    vs_t = np.einsum('...i,...i->...', Vs, n_t)
+    dp_dt = (n_t * vs[..., None] - n * vs_t[..., None]) / (vs ** 2)[..., None]
+    dp_perp = dp_dt[..., 0] * gs[..., 1] - dp_dt[..., 1] * gs[..., 0]
+    # receiver medium at the cell's own angle theta: dp/dtheta . (g_z, -g_x), which fixes Im M
+    # (n = (sin, cos), n_t = dn/dtheta = (cos, -sin), dv/dtheta = V . n_t)
+    sn, cn = np.sin(S.theta)[:, None, None], np.cos(S.theta)[:, None, None]
+    v0_t = Vx * cn - Vz * sn
+    dp0_x = (cn * v0 - sn * v0_t) / v0 ** 2
+    dp0_z = (-sn * v0 - cn * v0_t) / v0 ** 2
+    dp0_perp = dp0_x * gz - dp0_z * gx
+    # receiver medium: density and the qP phase velocity along +z (c0) per node
+    rho0 = S.rho[None, :, :]
+    lam, _ = _ch.qp_eigen(_ch.christoffel(S.a, np.array([0.0, 0.0, 1.0])))
+    c0 = np.sqrt(lam)[None, :, :]
+    out = []
+    for om in omegas:
+        kap = -2j * V0 / (om * beam_width ** 2)
+        db = b_perp + kap * G['bt']
+        dth = t_perp + kap * G['Tt']
+        M = (-dp_perp * dth / db).real + 1j * 2 * V0 * dp0_perp / (om * beam_width ** 2 * np.abs(db) ** 2)
+        amp = np.sqrt(rho0 * V0 / (S.rho_s * Vsn * db))
+        w = 1j * c0 ** 2 / (4 * np.pi * v0 ** 2) * S.dth
+        term = w * amp * np.exp(1j * om * (tau + 0.5 * M * b ** 2))
+        term = np.where(flag & np.isfinite(term), term, 0.0)
+        u = term.sum(axis=0)
+        out.append(u * (S.rho_s * S.c_ref ** 2) / (S.rho * c0[0] ** 2))
+    return np.stack(out)
+
+
 def arrivals(S, lab, kmax=8, kmah=False):
     """count (nz, nx) uint8, T (nz, nx, kmax) float64, A (nz, nx, kmax) float64, overflow flag;
     with kmah=True also M (nz, nx, kmax) int, each arrival's KMAH index: the number of caustics its

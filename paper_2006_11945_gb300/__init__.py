@@ -29,7 +29,8 @@ EGB_FP32_PHASE64, EGB_FP64 = 0, 1
 
 EXPORTED = ('egb_create', 'egb_destroy', 'egb_medium', 'egb_source', 'egb_evolve', 'egb_superpose',
             'egb_sync', 'egb_release', 'egb_last_error', 'egb_get_solve_info', 'egb_read_state',
-            'egb_read_velocity', 'egb_superpose_noalloc', 'egb_evolve_batch', 'egb_zmarch')
+            'egb_read_velocity', 'egb_superpose_noalloc', 'egb_evolve_batch', 'egb_zmarch',
+            'egb_superpose_receiver')
 
 
 class EgbError(RuntimeError):
@@ -75,11 +76,12 @@ def load(path: Optional[str] = None):
     lib.egb_create.argtypes = [P(vp), i, vp, P(egb_opts)]
     lib.egb_destroy.argtypes = [vp]
     lib.egb_medium.argtypes = [vp, i, P(i), P(d), P(d), vp, vp, P(u64)]
-    lib.egb_source.argtypes = [vp, u64, P(d), i, P(d), d, P(i), d, P(u64)]
+    lib.egb_source.argtypes = [vp, u64, P(d), i, P(d), d, P(i), d, d, P(u64)]
     lib.egb_evolve.argtypes = [vp, u64, i, d]
     lib.egb_evolve_batch.argtypes = [vp, i, P(u64), P(i), d]
     lib.egb_superpose.argtypes = [vp, u64, vp, vp, vp, vp, i]
     lib.egb_superpose_noalloc.argtypes = [vp, u64, vp, vp, vp, vp, i]
+    lib.egb_superpose_receiver.argtypes = [vp, u64, vp]
     lib.egb_sync.argtypes = [vp]
     lib.egb_release.argtypes = [vp, u64]
     lib.egb_last_error.argtypes = [vp]
@@ -142,13 +144,18 @@ def egb_medium(h, n, hsp, origin, c21, rho, dim=2):
     return out.value
 
 
-def egb_source(h, medium, xs, omegas: Sequence[float], beam_width, n_theta, r0=0.0, n_phi=0):
+def egb_source(h, medium, xs, omegas: Sequence[float], beam_width, n_theta, r0=0.0, n_phi=0, R_sigma=0.0):
     xs_ = (ctypes.c_double * 3)(*xs)
     om = (ctypes.c_double * len(omegas))(*omegas)
     na = (ctypes.c_int * 2)(n_theta, n_phi)
     out = ctypes.c_uint64()
-    _check(h, load().egb_source(h, medium, xs_, len(omegas), om, beam_width, na, r0, ctypes.byref(out)))
+    _check(h, load().egb_source(h, medium, xs_, len(omegas), om, beam_width, na, r0, R_sigma or 0.0,
+                                ctypes.byref(out)))
     return out.value
+
+
+def egb_superpose_receiver(h, solve, u_out):
+    _check(h, load().egb_superpose_receiver(h, solve, _ptr(u_out)))
 
 
 def egb_evolve(h, solve, steps, cfl):
@@ -245,7 +252,14 @@ class Context:
 
     def source_2d(self, medium, problem):
         return egb_source(self.h, medium, (problem.xs[0], 0.0, problem.xs[1]), problem.omegas,
-                          problem.beam_width, problem.n_theta, problem.r0 or 0.0)
+                          problem.beam_width, problem.n_theta, problem.r0 or 0.0,
+                          R_sigma=getattr(problem, 'R_sigma', None) or 0.0)
+
+    def superpose_receiver(self, solve, n_omega, nz, nx):
+        """egb_superpose_receiver into a host array (n_omega, nz, nx) complex64."""
+        u = np.zeros((n_omega, nz, nx), np.complex64)
+        egb_superpose_receiver(self.h, solve, u)
+        return u
 
     def evolve(self, solve, steps, cfl):
         egb_evolve(self.h, solve, steps, cfl)
@@ -276,7 +290,8 @@ class Context:
 
     def source_3d(self, medium, problem):
         return egb_source(self.h, medium, tuple(problem.xs), problem.omegas, problem.beam_width,
-                          problem.n_theta, problem.r0 or 0.0, n_phi=problem.n_phi)
+                          problem.n_theta, problem.r0 or 0.0, n_phi=problem.n_phi,
+                          R_sigma=getattr(problem, "R_sigma", None) or 0.0)
 
     def superpose_3d(self, solve, n_omega, nz, ny, nx, kmax=8):
         u = np.zeros((n_omega, nz, ny, nx), np.complex64)

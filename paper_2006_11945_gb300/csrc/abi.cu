@@ -138,7 +138,7 @@ egb_status ensure_desc(egb_ctx *c, int n) {
 
 // A point source in a 3-D medium (the 3-D path of egb_source).
 egb_status source3d(egb_ctx *c, uint64_t mid, Medium *m, const double xs[3], int n_omega, const double *omega,
-                    double beam_width, const int n_ang[2], double r0, egb_solve_id *out) {
+                    double beam_width, const int n_ang[2], double r0, double R_sigma, egb_solve_id *out) {
     int nth = n_ang[0], nph = n_ang[1];
     if (nth < 2 || nth > 512 || nph < 4 || nph > 1024 || nph % 2)
         return fail(c, EGB_E_INVALID, "3-D angles: n_theta in 2..512, n_phi even in 4..1024");
@@ -181,7 +181,7 @@ egb_status source3d(egb_ctx *c, uint64_t mid, Medium *m, const double xs[3], int
             far2 += fmax(a, b * b);
         }
     }
-    s->R_sigma = fmax(fmax(4.0 * s->r0, Lmin / 8.0), 2.0 * dA * sqrt(far2));
+    s->R_sigma = R_sigma > 0 ? fmax(R_sigma, s->r0) : fmax(fmax(4.0 * s->r0, Lmin / 8.0), 2.0 * dA * sqrt(far2));
     size_t cells = (size_t)g.nodes * nth * nph;
     size_t state_b = (size_t)NF3 * g.field * 4;
     s->bytes = 3 * state_b + cells * 9 * 4 + cells + (size_t)nth * nph * 24 + 32 * 4;
@@ -375,7 +375,7 @@ egb_status egb_medium(egb_ctx *c, int dim, const int n[3], const double h[3], co
 
 egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_omega,
                       const double *omega, double beam_width, const int n_ang[2], double r0,
-                      egb_solve_id *out) {
+                      double R_sigma, egb_solve_id *out) {
     if (!c) return EGB_E_INVALID;
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->media.find(mid);
@@ -385,7 +385,9 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     for (int i = 0; i < n_omega; ++i)
         if (!(omega[i] > 0)) return fail(c, EGB_E_INVALID, "omega must be > 0");
     if (!(beam_width > 0)) return fail(c, EGB_E_INVALID, "beam width must be > 0");
-    if (it->second->dim == 3) return source3d(c, mid, it->second, xs, n_omega, omega, beam_width, n_ang, r0, out);
+    if (R_sigma > 0 && r0 > 0 && R_sigma < r0) return fail(c, EGB_E_INVALID, "R_sigma must be at least r0");
+    if (it->second->dim == 3)
+        return source3d(c, mid, it->second, xs, n_omega, omega, beam_width, n_ang, r0, R_sigma, out);
     int nth = n_ang[0];
     if (nth < 8 || nth > 4096) return fail(c, EGB_E_INVALID, "n_theta must be in 8..4096");
     Medium *m = it->second;
@@ -461,7 +463,7 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
     {
         double Lx = (g.nx - 1) * g.hx, Lz = (g.nz - 1) * g.hz;
         double L8 = (Lx < Lz ? Lx : Lz) / 8.0;
-        s->R_sigma = 4.0 * s->r0 > L8 ? 4.0 * s->r0 : L8;
+        s->R_sigma = R_sigma > 0 ? fmax(R_sigma, s->r0) : (4.0 * s->r0 > L8 ? 4.0 * s->r0 : L8);
     }
     float *d_rate = nullptr;
     e = cudaMalloc(&d_rate, 4);
@@ -653,6 +655,40 @@ egb_status egb_superpose(egb_ctx *c, egb_solve_id sid, void *u_out, uint8_t *cou
     if (hT) cudaFree(dT);
     if (hA) cudaFree(dA);
     if (e != cudaSuccess) return cuda_fail(c, e, "superpose");
+    return EGB_OK;
+}
+
+egb_status egb_superpose_receiver(egb_ctx *c, egb_solve_id sid, void *u_out) {
+    if (!c) return EGB_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->solves3d.count(sid)) return fail(c, EGB_E_INVALID, "the receiver-side reduction takes 2-D solves");
+    auto it = c->solves.find(sid);
+    if (it == c->solves.end()) return fail(c, EGB_E_INVALID, "unknown solve id");
+    if (!u_out) return fail(c, EGB_E_INVALID, "u_out is required");
+    Solve *s = it->second;
+    if (s->omega.empty()) return fail(c, EGB_E_INVALID, "the solve has no frequencies");
+    DeviceGuard dg(c->device);
+    size_t need = superpose_scratch_bytes(*s);
+    cudaError_t e = cudaSuccess;
+    if (s->scratch_bytes < need) {
+        cudaFree(s->scratch);
+        s->scratch = nullptr;
+        s->scratch_bytes = 0;
+        e = cudaMalloc(&s->scratch, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, EGB_E_NOMEM, "superposition scratch (%zu bytes)", need); }
+        s->scratch_bytes = need;
+    }
+    const Grid2D &g = s->g;
+    size_t ub = s->omega.size() * (size_t)g.nx * g.nz * 8;
+    void *du = u_out;
+    bool hu = !is_device_ptr(u_out);
+    if (hu) e = cudaMalloc(&du, ub);
+    if (e == cudaSuccess && s->fp64) e = fp64_to_fp32_state(*s, c->stream);
+    if (e == cudaSuccess) e = launch_superpose_receiver(*s, (float2 *)du, c->d_err, c->stream);
+    if (e == cudaSuccess && hu) e = cudaMemcpyAsync(u_out, du, ub, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && hu) e = cudaStreamSynchronize(c->stream);
+    if (hu) cudaFree(du);
+    if (e != cudaSuccess) return cuda_fail(c, e, "receiver-side superpose");
     return EGB_OK;
 }
 

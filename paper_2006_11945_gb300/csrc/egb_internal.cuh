@@ -107,6 +107,11 @@ struct Medium {
     size_t bytes = 0;
 };
 
+// A solve's source block (floats, device): [0,21) a_s, [21] rho_s, [22] c_ref, [23] pad,
+// [24 + 2k] psx_k, [25 + 2k] psz_k (slowness at the source), [24 + 2 nth + 2k] sin, cos theta_k
+__host__ __device__ inline int src_ps(int k) { return 24 + 2 * k; }
+__host__ __device__ inline int src_sc(int nth, int k) { return 24 + 2 * nth + 2 * k; }
+
 struct Solve {
     uint64_t medium_id;
     Medium *m;
@@ -227,6 +232,8 @@ cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cud
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 size_t superpose_scratch_bytes(const Solve &sv);
+// Receiver-side (reciprocal) reduction of the solve's labels into u_dev [n_omega][nz][nx].
+cudaError_t launch_superpose_receiver(Solve &sv, float2 *u_dev, unsigned *d_err, cudaStream_t s);
 // Device address of the fixed superposition scratch (EGB_NOALLOC_SCRATCH_BYTES) on `device`, which
 // must be the current device; looked up once per device.
 cudaError_t noalloc_scratch(int device, void **ptr);

@@ -157,7 +157,11 @@ __device__ __forceinline__ float2 weno3_2(const float2 d[4], const Up2 &up, floa
     float2 B2 = mul2(B, B);
     float2 den = fma2(mul2(A, A), f2(2.f, 2.f), B2);
     float2 num = mul2(B2, up.sig);
-    float2 w = f2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    // w = num / den with one approximate reciprocal per lane and one packed multiply
+    float rx, ry;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(den.y));
+    float2 w = mul2(num, f2(rx, ry));
     return fma2(w, sub2(E, e1), add2(d[1], d[2]));
 }
 

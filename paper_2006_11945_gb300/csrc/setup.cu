@@ -93,10 +93,7 @@ cudaError_t launch_medium_prep(const Medium &m, const float *c21_dev, const floa
 }
 
 // ------------------------------- source block ---------------------------------------------------
-// src layout (floats): [0,21) a_s, [21] rho_s, [22] c_ref, [23] pad,
-//                      [24 + 2k] psx_k, [25 + 2k] psz_k, [24 + 2 nth + 2k] sin, cos theta_k
-__host__ __device__ inline int src_ps(int k) { return 24 + 2 * k; }
-__host__ __device__ inline int src_sc(int nth, int k) { return 24 + 2 * nth + 2 * k; }
+// the source block's layout: src_ps, src_sc in egb_internal.cuh
 
 __device__ void bilinear_weights(const Medium &m, double xs, double zs, int &ix, int &iz, double &tx,
                                  double &tz) {

@@ -409,6 +409,89 @@ __global__ void k_sum(SupArgs A, float2 *u) {
     }
 }
 
+// Receiver-side (reciprocal) reduction of the same labels (Eq. 34 read from the receiver): at
+// receiver x0, a Gaussian beam launched back along every source-labelled ray through x0 (cells
+// (x0, theta) with q > 1/2, not frozen), evaluated at x_s.  The label Jacobian at x0 carries the
+// launch perturbation (dx_perp, dtheta) = (1, kappa0), kappa0 = -2 i |V0| / (omega w0^2), to the
+// ray's closest approach C: db = b_perp + kappa0 b_theta, dvartheta = vartheta_perp +
+// kappa0 vartheta_theta (perp along (g_z, -g_x), g the unit group direction at x0).  At C the
+// reversed beam's Hessian is M = -(dp/dvartheta . (g_z, -g_x))_source dvartheta / db and its phase at
+// x_s is tau + M b^2 / 2.  Im M comes from the beam's Wronskian, which the symplectic ray propagator
+// keeps: Im M = 2 |V0| (dp/dtheta . (g_z, -g_x))_x0 / (omega w0^2 |db|^2) (the label Jacobian
+// meets this only up to discretisation error, and near the edge of the source-ray tube its Im M can
+// vanish at a small |db|, leaving an undamped term whose phase hangs on the labels' last digits).
+// Amplitude sqrt(rho0 |V0| / (rho_s |V_s(vartheta)| db)) (principal root: rays without a
+// caustic), weight i c0^2 / (4 pi v0^2) dtheta, and the sum rescaled by
+// rho_s c_s^2 / (rho0 c0^2) to the source side's normalisation (reciprocity).  Lanes split the
+// angles of a receiver as in k_sum.
+__global__ void k_sum_receiver(SupArgs A, const float *__restrict__ med_a, float2 *u) {
+    const Grid2D &g = A.g;
+    __shared__ float as[21];
+    if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, t = lane % SUM_LANES;
+    const int ix = blockIdx.x * (blockDim.x / SUM_LANES) + threadIdx.x / SUM_LANES;
+    const int iz = blockIdx.y;
+    const bool rx = ix < g.nx;
+    const int ixc = rx ? ix : g.nx - 1;
+    const int64_t node = (int64_t)iz * g.nx + ixc, nodes = (int64_t)g.nx * g.nz;
+    float a0[21];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) a0[c] = med_a[c * nodes + node];
+    const float c0 = source_velocity(a0, 0.f, 1.f).v;  // qP phase velocity along +z at x0
+    const float rho0 = A.rho[node], rho_s = A.src[21], c_s = A.src[22];
+    const float four_pi = 12.5663706143591729f;
+    for (int w = 0; w < A.n_omega; ++w) {
+        double om = A.omega_dev[w];
+        float omf = (float)om, ohi = omf, olo = (float)(om - (double)ohi);
+        float kap = -2.f / (omf * A.w0 * A.w0);  // kappa0 / (i |V0|)
+        float are = 0.f, aim = 0.f;
+        for (int k = t; k < g.nth; k += SUM_LANES) {
+            int64_t o = cidx(g, k, iz, ixc);
+            if (!A.FL[o]) continue;
+            CellData d = load_cell(A, k, iz, ixc);
+            float b = A.B[o];
+            float V0 = hypotf(d.Vx, d.Vz), gx = d.Vx / V0, gz = d.Vz / V0;
+            float b_perp = d.bx * gz - d.bz * gx, t_perp = d.tx * gz - d.tz * gx;
+            float sth, cth;
+            sincosf(d.th, &sth, &cth);
+            SrcVel sv = source_velocity(as, sth, cth);
+            float vs_t = sv.Vx * cth - sv.Vz * sth;
+            float iv2 = 1.f / (sv.v * sv.v);
+            float dpx = (cth * sv.v - sth * vs_t) * iv2, dpz = (-sth * sv.v - cth * vs_t) * iv2;
+            float dp_perp = (dpx * sv.Vz - dpz * sv.Vx) / sv.Vn;
+            // receiver medium at the cell's own angle: dp/dtheta . (g_z, -g_x) fixes Im M through
+            // the beam's Wronskian (the label Jacobian keeps it only up to discretisation error)
+            const float s0 = A.src[src_sc(g.nth, k)], c0k = A.src[src_sc(g.nth, k) + 1];
+            float v0_t = d.Vx * c0k - d.Vz * s0, iv02 = 1.f / (d.v * d.v);
+            float dp0x = (c0k * d.v - s0 * v0_t) * iv02, dp0z = (-s0 * d.v - c0k * v0_t) * iv02;
+            float dp0_perp = dp0x * gz - dp0z * gx;
+            cf db = {b_perp, kap * V0 * d.bt}, dth = {t_perp, kap * V0 * d.tt};
+            cf M = cdiv(dth, db);
+            M = {-dp_perp * M.re, -kap * V0 * dp0_perp / (db.re * db.re + db.im * db.im)};
+            cf amp = csqrt_pr(cdiv(cf{rho0 * V0 / (rho_s * sv.Vn), 0.f}, db));
+            float wgt = g.dth * c0 * c0 / (four_pi * d.v * d.v);
+            float ph = phase_mod(ohi, olo, d.tau_hi, d.tau_lo, A.C1, A.C2, A.C3) + 0.5f * omf * M.re * b * b;
+            float dec = -0.5f * omf * M.im * b * b;
+            if (!(dec > -60.f)) continue;  // far outside the beam (or not finite)
+            float mag = wgt * __expf(dec), sp, cp;
+            sincosf(ph, &sp, &cp);
+            // i * mag * amp * exp(i ph)
+            cf e = cmul(amp, cf{cp, sp});
+            if (!(isfinite(e.re) && isfinite(e.im))) continue;
+            are -= mag * e.im;
+            aim += mag * e.re;
+        }
+#pragma unroll
+        for (int m = SUM_LANES / 2; m > 0; m >>= 1) {
+            are += __shfl_xor_sync(0xffffffffu, are, m);
+            aim += __shfl_xor_sync(0xffffffffu, aim, m);
+        }
+        float sc = rho_s * c_s * c_s / (rho0 * c0 * c0);
+        if (rx && t == 0) u[((int64_t)w * g.nz + iz) * g.nx + ix] = make_float2(sc * are, sc * aim);
+    }
+}
+
 constexpr int KMAX_LIMIT = 32;
 
 __global__ void k_arrivals(SupArgs A, uint8_t *count, double *T, float *Aout, int kmax) {
@@ -497,8 +580,39 @@ static void split_two_pi(float &C1, float &C2, float &C3) {
     C3 = (float)(two_pi - c1 - c2);
 }
 
+static cudaError_t superpose_args(Solve &sv, unsigned *d_err, cudaStream_t s, SupArgs &A);
+
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s) {
+    SupArgs A;
+    cudaError_t e = superpose_args(sv, d_err, s, A);
+    if (e != cudaSuccess) return e;
+    const Grid2D &g = sv.g;
+    dim3 gb((g.nx + 127) / 128, g.nz, g.nth);
+    k_beam_fields<<<gb, 128, 0, s>>>(A);
+    if (u_dev) {
+        k_centres<true><<<dim3((g.nz + 63) / 64, g.nth), 64, 0, s>>>(A);
+        k_centres<false><<<dim3((g.nx + 63) / 64, g.nth), 64, 0, s>>>(A);
+        k_sum<<<dim3((g.nx + 256 / SUM_LANES - 1) / (256 / SUM_LANES), g.nz), 256, 0, s>>>(A, u_dev);
+    }
+    if (count_dev || T_dev || A_dev)
+        k_arrivals<<<dim3((g.nx + 63) / 64, g.nz), 64, 0, s>>>(A, count_dev, T_dev, A_dev, kmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_superpose_receiver(Solve &sv, float2 *u_dev, unsigned *d_err, cudaStream_t s) {
+    SupArgs A;
+    cudaError_t e = superpose_args(sv, d_err, s, A);
+    if (e != cudaSuccess) return e;
+    const Grid2D &g = sv.g;
+    dim3 gb((g.nx + 127) / 128, g.nz, g.nth);
+    k_beam_fields<<<gb, 128, 0, s>>>(A);
+    k_sum_receiver<<<dim3((g.nx + 256 / SUM_LANES - 1) / (256 / SUM_LANES), g.nz), 256, 0, s>>>(A, sv.m->a, u_dev);
+    return cudaGetLastError();
+}
+
+// Arguments of the superposition kernels: scratch carved from the solve's superposition scratch.
+static cudaError_t superpose_args(Solve &sv, unsigned *d_err, cudaStream_t s, SupArgs &A) {
     const Grid2D &g = sv.g;
     size_t cells = (size_t)g.nth * g.nx * g.nz;
     size_t rs = (size_t)g.nth * g.nz * KC, cs = (size_t)g.nth * g.nx * KC;
@@ -509,7 +623,6 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
         base += (bytes + 255) & ~(size_t)255;
         return (void *)p;
     };
-    SupArgs A;
     A.g = g;
     A.st = sv.fp64 ? sv.state[0] : sv.state[sv.cur];  // the FP64 form converts into buffer 0
     A.vel = sv.vel;
@@ -537,16 +650,7 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
     A.frozen = sv.frozen;
     split_two_pi(A.C1, A.C2, A.C3);
     A.err = d_err;
-    dim3 gb((g.nx + 127) / 128, g.nz, g.nth);
-    k_beam_fields<<<gb, 128, 0, s>>>(A);
-    if (u_dev) {
-        k_centres<true><<<dim3((g.nz + 63) / 64, g.nth), 64, 0, s>>>(A);
-        k_centres<false><<<dim3((g.nx + 63) / 64, g.nth), 64, 0, s>>>(A);
-        k_sum<<<dim3((g.nx + 256 / SUM_LANES - 1) / (256 / SUM_LANES), g.nz), 256, 0, s>>>(A, u_dev);
-    }
-    if (count_dev || T_dev || A_dev)
-        k_arrivals<<<dim3((g.nx + 63) / 64, g.nz), 64, 0, s>>>(A, count_dev, T_dev, A_dev, kmax);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace egb

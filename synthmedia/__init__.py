@@ -163,6 +163,7 @@ class Problem2D:
     cfl: float = 0.5
     r0: Optional[float] = None   # frozen source-ball radius (m); default 2*max(hx, hz)
     origin: Tuple[float, float] = (0.0, 0.0)
+    R_sigma: Optional[float] = None   # closest-approach disc radius (m); default max(4 r0, min(L)/8)
     meta: dict = field(default_factory=dict)
 
     @property

@@ -116,3 +116,84 @@ def test_heterogeneous_wavefield_is_bounded():
     u = SP.green(S, lab, p.omegas, p.beam_width)
     assert np.all(np.isfinite(u))
     assert np.max(np.abs(u)) < 1.0
+
+
+# ---- receiver-side (reciprocal) reduction of the same labels (Eq. 34 read through reciprocity) ----
+
+def _wide_tube(p, R_sigma):
+    import dataclasses
+    return _exact_setup(dataclasses.replace(p, R_sigma=R_sigma))
+
+
+@pytest.fixture(scope='module')
+def iso_wide():
+    """The isotropic medium with a 400 m source-ray tube: the receiver-side beams reach x_s about
+    w(r) = w0 sqrt(1 + (2 r / (k w0^2))^2) wide (143 m at 640 m, 60 Hz, w0 = 100 m) and need the
+    labels of rays up to about 2 w(r) from the source."""
+    p = synthmedia.isotropic_homogeneous(n=128, h=10.0, n_theta=384, freqs=[60.0])
+    return (p,) + _wide_tube(p, 400.0)
+
+
+def test_receiver_side_hankel_convergence(iso_wide):
+    p, S, lab, X, Z, edge = iso_wide
+    om = 2 * math.pi * 60.0
+    k = om / p.meta['vp']
+    r = np.hypot(X, Z)
+    ref = CF.hankel_green_2d(k, np.where(r > 0, r, 1.0))
+    u = SP.green_receiver(S, lab, [om], 100.0)[0]
+    err = _band_errors(u, ref, k * r, edge > 0.25 * 128 * 10.0, [(5, 10), (10, 20), (20, 40), (40, 80)])
+    print('receiver-side vs (i/4) H0 by kr band', err)
+    assert np.all(np.diff(err) < 0) and err[2] < 0.01 and err[3] < 0.01, err
+
+
+def test_receiver_side_beam_width_independence(iso_wide):
+    p, S, lab, X, Z, edge = iso_wide
+    om = 2 * math.pi * 60.0
+    k = om / p.meta['vp']
+    r = np.hypot(X, Z)
+    u1, u2 = (SP.green_receiver(S, lab, [om], w)[0] for w in (100.0, 150.0))
+    m = (edge > 0.25 * 128 * 10.0) & (k * r >= 20) & (k * r < 80)
+    assert np.linalg.norm(u1[m] - u2[m]) / np.linalg.norm(u1[m]) < 0.02
+
+
+def test_receiver_side_vti_far_field(vti):
+    """VTI: the receiver-side sum of the closed-form labels (tube widened to 400 m) against the
+    stationary-phase evaluation of the exact plane-wave integral, and against the source-side sum."""
+    p0 = vti[0]
+    p, S, lab, X, Z, edge = (p0,) + _wide_tube(p0, 400.0)
+    m = p.meta
+    om = 2 * math.pi * 60.0
+    v_of = lambda th: CF.thomsen_vti_phase_velocity(th, m['vp0'], m['vs0'], m['eps'], m['delta'])
+    V_of = lambda th: CF.vti_group_velocity(th, m['vp0'], m['vs0'], m['eps'], m['delta'])[1:]
+    r = np.hypot(X, Z)
+    sel = (edge > 0.25 * 128 * 10.0) & (r > 350.0)
+    ref, T, _ = CF.homogeneous_go_green(X[sel], Z[sel], 0.0, 0.0, om, v_of, V_of, m['vp0'])
+    ur = SP.green_receiver(S, lab, [om], 100.0)[0][sel]
+    us = SP.green(S, lab, [om], 100.0)[0][sel]
+    assert np.linalg.norm(ur - ref) / np.linalg.norm(ref) < 0.015
+    assert np.linalg.norm(ur - us) / np.linalg.norm(us) < 0.03
+
+
+@pytest.mark.slow
+def test_receiver_side_agrees_with_source_side_in_a_heterogeneous_medium():
+    """TTI (64^2 at 40 m, 96 angles) with a 900 m source-ray tube: at receivers 200-600 m from
+    the source, well inside the tube, the two reductions of the same labels agree as the frequency
+    grows.  (Beyond the frozen disc's radius they part: the disc's straight-ray closest-approach
+    data are only accurate where the medium varies little across it.)"""
+    import dataclasses
+    p = synthmedia.tti_heterogeneous(n=64, n_theta=96, length=2560.0, steps=400, freqs=(20.0, 40.0, 80.0),
+                                     beam_width=150.0)
+    p = dataclasses.replace(p, R_sigma=900.0)
+    S, st, dt = L.evolve(p)
+    lab = L.interior_state(st, S)
+    us = SP.green(S, lab, p.omegas, p.beam_width)
+    ur = SP.green_receiver(S, lab, p.omegas, p.beam_width)
+    x = np.arange(p.nx) * p.hx - p.xs[0]
+    z = np.arange(p.nz) * p.hz - p.xs[1]
+    Z, X = np.meshgrid(z, x, indexing='ij')
+    r = np.hypot(X, Z)
+    m = (r >= 200) & (r < 600)
+    e = [np.linalg.norm(ur[w][m] - us[w][m]) / np.linalg.norm(us[w][m]) for w in range(3)]
+    med = [np.median(np.abs(ur[w][m] / us[w][m] - 1)) for w in range(3)]
+    print('receiver vs source side, L2', e, 'median', med)
+    assert e[1] < 0.1 and e[2] < 0.1 and med[2] < med[0] and med[2] < 0.06
