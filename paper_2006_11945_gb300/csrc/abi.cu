@@ -122,6 +122,11 @@ egb_status latched(egb_ctx *c) {
 }
 
 egb_status ensure_desc(egb_ctx *c, int n) {
+    if (!c->d_tail && cudaMalloc(&c->d_tail, tail_plan_bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_tail = nullptr;
+        return fail(c, EGB_E_NOMEM, "stage work split");
+    }
     if (c->desc_cap >= n) return EGB_OK;
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_desc);
@@ -306,6 +311,7 @@ egb_status egb_destroy(egb_ctx *c) {
         c->media.clear();
         cudaFree(c->d_err);
         cudaFree(c->d_desc);
+        cudaFree(c->d_tail);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     }
     delete c;
@@ -511,7 +517,7 @@ egb_status egb_source(egb_ctx *c, egb_medium_id mid, const double xs[3], int n_o
         if (it != c->tuned_chunk.end()) {
             tma_set_chunk(*s, it->second);
         } else {
-            e = tma_autotune(*s, c->d_desc, c->d_err, c->stream);
+            e = tma_autotune(*s, c->d_desc, c->d_tail, c->d_err, c->stream);
             if (e != cudaSuccess) { free_solve(s); return cuda_fail(c, e, "stencil autotuning"); }
             c->tuned_chunk[shape] = tma_chunk(*s);
         }
@@ -556,7 +562,7 @@ egb_status egb_evolve(egb_ctx *c, egb_solve_id sid, int steps, double cfl) {
         egb_status st = ensure_desc(c, 1);
         if (st != EGB_OK) return st;
         Solve *one[1] = {s};
-        cudaError_t e = evolve_batch(one, 1, steps, c->d_desc, c->d_err, c->stream, c->cap_stream);
+        cudaError_t e = evolve_batch(one, 1, steps, c->d_desc, c->d_tail, c->d_err, c->stream, c->cap_stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "evolve launch");
     }
     s->steps += steps;
@@ -595,7 +601,7 @@ egb_status egb_evolve_batch(egb_ctx *c, int n, const egb_solve_id *ids, const in
                 m = (m == 0 || left[i] < m) ? left[i] : m;
             }
         if (act.empty()) break;
-        cudaError_t e = evolve_batch(act.data(), (int)act.size(), m, c->d_desc, c->d_err, c->stream, c->cap_stream);
+        cudaError_t e = evolve_batch(act.data(), (int)act.size(), m, c->d_desc, c->d_tail, c->d_err, c->stream, c->cap_stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched evolve");
         for (int i = 0; i < n; ++i)
             if (left[i] > 0) {

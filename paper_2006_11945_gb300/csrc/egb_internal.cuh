@@ -202,6 +202,7 @@ struct Ctx {
     unsigned *d_err = nullptr;  // device error bits
     StageDesc *d_desc = nullptr;  // stage descriptors of batched launches (device)
     int desc_cap = 0;             // capacity in solves (9 descriptors per solve)
+    void *d_tail = nullptr;       // the stage launches' tail work split (device, tail_plan_bytes())
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture CUDA graphs
     // theta chunk chosen by the stencil autotuner, per grid shape (nx, nz, n_theta): later solves
     // of the same shape reuse it instead of timing the candidates again
@@ -222,10 +223,11 @@ cudaError_t launch_zero_frozen_velocity(const Solve &sv, cudaStream_t s);
 cudaError_t tma_prepare(Solve &sv);
 void tma_release(Solve &sv);
 size_t stage_desc_bytes();
+size_t tail_plan_bytes();
 int tma_chunk(const Solve &sv);
 void tma_set_chunk(Solve &sv, int chunk);
-cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s);
-cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
+cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, void *d_tail, unsigned *err, cudaStream_t s);
+cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, void *d_tail, unsigned *err, cudaStream_t s,
                          cudaStream_t cap);
 // One sample of the continued spreading argument from the padded FP32 state st (init: first sample).
 cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cudaStream_t s);

@@ -27,6 +27,7 @@ constexpr int TX = 64, TZ = 6;                     // tile (cells)
 constexpr int HX = TX + 8, HZ = TZ + 4;            // halo box (x -4..67, z -2..TZ+1)
 constexpr int RING = 6, RING2 = 2;                 // plane slots, centre-plane slots
 constexpr int CTAS_PER_SM = 2;                     // two CTAs resident per SM (shared memory < 114 KB each)
+constexpr int TAIL_SEGS_PER_CTA = 2;               // capacity of the tail work split (segments per CTA)
 constexpr int HALO_FLOATS = NFIELD * HZ * HX;      // floats one halo copy brings
 constexpr int UN_FLOATS = NFIELD * TZ * TX;        // floats of the u^n copy
 constexpr int V_FLOATS = 3 * TZ * TX;              // floats of the velocity copy
@@ -186,7 +187,8 @@ __device__ __forceinline__ float2 deriv2_ff(const float2 h[5], const float2 l[5]
 // instead of the default one; a separate instantiation keeps the default kernel free of it.
 template <int STAGE, bool BOUNDED>
 __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
-    k_rk3_tma(const StageDesc *__restrict__ D, int nsolves, int total_items, unsigned *err) {
+    k_rk3_tma(const StageDesc *__restrict__ D, int nsolves, int full_items, const int4 *__restrict__ tail,
+              const int *__restrict__ tail_begin, unsigned *err) {
     using namespace tma;
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = reinterpret_cast<float *>(smem);
@@ -207,8 +209,22 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
     const uint32_t bytes_halo = HALO_FLOATS * 4;
     const uint32_t bytes2 = (STAGE == 1 ? V_FLOATS : UN_FLOATS + V_FLOATS) * 4;
     int si = 0;
+    // work: the strided items b, b + G, ... below full_items, then this CTA's tail segments
+    // (item, first plane within the item, plane count), in increasing item order
+    const int b = blockIdx.x;
+    const int nfull = b < full_items ? (full_items - 1 - b) / (int)gridDim.x + 1 : 0;
+    const int t0 = tail_begin[b], nwork = nfull + tail_begin[b + 1] - t0;
 
-    for (int gitem = blockIdx.x; gitem < total_items; gitem += gridDim.x) {
+    for (int q = 0; q < nwork; ++q) {
+        int gitem, k_off = 0, k_len = 1 << 30;
+        if (q < nfull) {
+            gitem = b + q * (int)gridDim.x;
+        } else {
+            const int4 sg = tail[t0 + q - nfull];
+            gitem = sg.x;
+            k_off = sg.y;
+            k_len = sg.z;
+        }
         while (si + 1 < nsolves && gitem >= D[si + 1].item_begin) ++si;
         const StageDesc &A = D[si];
         // the descriptor's scalars live in registers for the whole item (the mbarrier waits'
@@ -227,8 +243,8 @@ __global__ void __launch_bounds__(tma::THREADS, tma::CTAS_PER_SM)
         int rest = item / A.tiles_x;
         int zt = rest % A.tiles_z;
         int ch = rest / A.tiles_z;
-        int k0 = ch * A.chunk;
-        int kn = min(A.chunk, nth - k0);
+        int k0 = ch * A.chunk + k_off;
+        int kn = min(min(A.chunk, nth - ch * A.chunk) - k_off, k_len);
         int x0 = xt * TX, z0 = zt * TZ;
         int nplanes = kn + 4;
         auto plane_of = [&](int j) { return (k0 - 2 + j + 2 * nth) % nth; };
@@ -511,21 +527,101 @@ static StageDesc make_desc(const Solve &sv, int stage, int r, int chunk) {
     return A;
 }
 
-static void launch_stage(int stage, const StageDesc *d, int nsolves, int total, unsigned *err, cudaStream_t s,
-                         bool bounded) {
-    int sms = sm_count() * tma::CTAS_PER_SM;
-    int grid = total < sms ? total : sms;
+// Work split of a stage launch over its G = 2 x SMs CTAs.  The items (x tile, z tile, theta chunk)
+// of the launch's solves, numbered in solve order, are strided over the CTAs (CTA b takes items
+// b, b + G, ...) for the full rounds; the planes of the items of the last, partial round are cut
+// into G contiguous runs of equal length, one per CTA.  (The 512^2 x 256 solve has 2752 items of
+// 64 planes: nine rounds of 304 and 16 left over, which would otherwise run on 16 CTAs.  Measured:
+// 0.5 % per stage launch; re-splitting the last two rounds instead was 0.5 % slower than plain
+// striding.)  Launches with at most G items give each CTA one item.  Device layout: int4 segments [TAIL_SEGS_PER_CTA * G] (item, first
+// plane in the item, planes, unused), then int begin[G + 1] (CTA b's segments are
+// begin[b] .. begin[b + 1] - 1).
+struct TailPlan {
+    int grid = 0, full = 0;
+    std::vector<int4> segs;
+    std::vector<int> begin;
+};
+
+static int grid_ctas() { return sm_count() * tma::CTAS_PER_SM; }
+
+size_t tail_plan_bytes() {
+    size_t G = (size_t)grid_ctas();
+    return tma::TAIL_SEGS_PER_CTA * G * sizeof(int4) + (G + 1) * sizeof(int);
+}
+
+// planes of item `gi` (a global item number) of the launch described by descs[0 .. n)
+static int item_planes(const StageDesc *descs, int n, int gi) {
+    int i = 0;
+    while (i + 1 < n && gi >= descs[i + 1].item_begin) ++i;
+    const StageDesc &d = descs[i];
+    int ch = (gi - d.item_begin) / (d.tiles_x * d.tiles_z);
+    int kn = d.g.nth - ch * d.chunk;
+    return kn < d.chunk ? kn : d.chunk;
+}
+
+static TailPlan plan_tail(const StageDesc *descs, int n, int total) {
+    TailPlan P;
+    const int G = grid_ctas();
+    P.begin.assign((size_t)G + 1, 0);
+    P.grid = total < G ? total : G;
+    P.full = total;
+    if (total <= G) return P;
+    P.full = (total / G) * G;
+    if (P.full == total) return P;
+    std::vector<int64_t> pre(1, 0);  // plane prefix over the remaining items
+    for (int gi = P.full; gi < total; ++gi) pre.push_back(pre.back() + item_planes(descs, n, gi));
+    const int64_t planes = pre.back();
+    size_t it = 0;
+    for (int cta = 0; cta < G; ++cta) {
+        P.begin[cta] = (int)P.segs.size();
+        int64_t lo = planes * cta / G, hi = planes * (cta + 1) / G;
+        while (lo < hi) {
+            while (pre[it + 1] <= lo) ++it;
+            int64_t off = lo - pre[it], len = pre[it + 1] - lo;
+            if (len > hi - lo) len = hi - lo;
+            P.segs.push_back(make_int4(P.full + (int)it, (int)off, (int)len, 0));
+            lo += len;
+        }
+    }
+    P.begin[G] = (int)P.segs.size();
+    if (P.segs.size() > (size_t)tma::TAIL_SEGS_PER_CTA * G) {  // cannot happen (< G items left); keep strides
+        P.full = total;
+        P.segs.clear();
+        P.begin.assign((size_t)G + 1, 0);
+    }
+    return P;
+}
+
+static cudaError_t upload_tail(const TailPlan &P, void *d_tail, cudaStream_t s) {
+    const int G = grid_ctas();
+    char *base = (char *)d_tail;
+    cudaError_t e = cudaSuccess;
+    if (!P.segs.empty())
+        e = cudaMemcpyAsync(base, P.segs.data(), P.segs.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + tma::TAIL_SEGS_PER_CTA * (size_t)G * sizeof(int4), P.begin.data(),
+                            P.begin.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    return e;
+}
+
+static void launch_stage(int stage, const StageDesc *d, int nsolves, const TailPlan &P, void *d_tail,
+                         unsigned *err, cudaStream_t s, bool bounded) {
+    const int grid = P.grid;
     if (grid < 1) return;
+    const int G = grid_ctas();
+    const int4 *tail = (const int4 *)d_tail;
+    const int *tb = (const int *)((const char *)d_tail + tma::TAIL_SEGS_PER_CTA * (size_t)G * sizeof(int4));
     const int T = tma::THREADS;
     const size_t M = tma::SMEM_BYTES;
+    const int full = P.full;
     if (!bounded) {
-        if (stage == 1) k_rk3_tma<1, false><<<grid, T, M, s>>>(d, nsolves, total, err);
-        if (stage == 2) k_rk3_tma<2, false><<<grid, T, M, s>>>(d, nsolves, total, err);
-        if (stage == 3) k_rk3_tma<3, false><<<grid, T, M, s>>>(d, nsolves, total, err);
+        if (stage == 1) k_rk3_tma<1, false><<<grid, T, M, s>>>(d, nsolves, full, tail, tb, err);
+        if (stage == 2) k_rk3_tma<2, false><<<grid, T, M, s>>>(d, nsolves, full, tail, tb, err);
+        if (stage == 3) k_rk3_tma<3, false><<<grid, T, M, s>>>(d, nsolves, full, tail, tb, err);
     } else {
-        if (stage == 1) k_rk3_tma<1, true><<<grid, T, M, s>>>(d, nsolves, total, err);
-        if (stage == 2) k_rk3_tma<2, true><<<grid, T, M, s>>>(d, nsolves, total, err);
-        if (stage == 3) k_rk3_tma<3, true><<<grid, T, M, s>>>(d, nsolves, total, err);
+        if (stage == 1) k_rk3_tma<1, true><<<grid, T, M, s>>>(d, nsolves, full, tail, tb, err);
+        if (stage == 2) k_rk3_tma<2, true><<<grid, T, M, s>>>(d, nsolves, full, tail, tb, err);
+        if (stage == 3) k_rk3_tma<3, true><<<grid, T, M, s>>>(d, nsolves, full, tail, tb, err);
     }
 }
 
@@ -537,7 +633,7 @@ void tma_set_chunk(Solve &sv, int chunk) {
 
 // Autotuner: time stage 1 (reads u^n, writes a stage buffer, so the state is untouched) for each
 // theta-chunk candidate and keep the fastest.  Synchronises the stream.
-cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream_t s) {
+cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, void *d_tail, unsigned *err, cudaStream_t s) {
     static const int cand[4] = {8, 16, 32, 64};
     float best = 1e30f;
     int best_chunk = 8;
@@ -549,10 +645,13 @@ cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream
         if (ch > sv.g.nth && ci > 0) break;
         StageDesc h = make_desc(sv, 1, 0, ch);
         cudaMemcpyAsync(d_desc, &h, sizeof h, cudaMemcpyHostToDevice, s);
+        TailPlan P = plan_tail(&h, 1, h.items);
+        cudaError_t eu = upload_tail(P, d_tail, s);
+        if (eu != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return eu; }
         bool bounded = sv.wait_polls != 0;
-        launch_stage(1, d_desc, 1, h.items, err, s, bounded);  // warm
+        launch_stage(1, d_desc, 1, P, d_tail, err, s, bounded);  // warm
         cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) launch_stage(1, d_desc, 1, h.items, err, s, bounded);
+        for (int rep = 0; rep < 3; ++rep) launch_stage(1, d_desc, 1, P, d_tail, err, s, bounded);
         cudaEventRecord(e1, s);
         cudaError_t er = cudaEventSynchronize(e1);
         if (er != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return er; }
@@ -571,8 +670,8 @@ cudaError_t tma_autotune(Solve &sv, StageDesc *d_desc, unsigned *err, cudaStream
 // launched directly.  After every step whose count (sv->steps, the steps before this call, plus the
 // steps taken in it) is a multiple of BRANCH_SAMPLE, the solve's continued spreading argument is
 // sampled.  d_desc must hold 9 * n descriptors; cap is a non-legacy stream for capture.
-cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsigned *err, cudaStream_t s,
-                         cudaStream_t cap) {
+cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, void *d_tail, unsigned *err,
+                         cudaStream_t s, cudaStream_t cap) {
     if (n <= 0 || steps <= 0) return cudaSuccess;
     std::vector<StageDesc> h((size_t)9 * n);
     int total[9];
@@ -590,12 +689,16 @@ cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, unsign
         }
     cudaError_t e = cudaMemcpyAsync(d_desc, h.data(), h.size() * sizeof(StageDesc), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
+    // the items (and so the work split) are the same for every stage and rotation phase
+    const TailPlan P = plan_tail(h.data(), n, total[0]);
+    e = upload_tail(P, d_tail, s);
+    if (e != cudaSuccess) return e;
     bool bounded = false;  // any solve with a caller-set wait bound (they share their context's)
     for (int i = 0; i < n; ++i) bounded = bounded || sv[i]->wait_polls != 0;
     auto run_step = [&](int r, cudaStream_t st) {
         for (int stage = 1; stage <= 3; ++stage) {
             int slot = r * 3 + (stage - 1);
-            launch_stage(stage, d_desc + (size_t)slot * n, n, total[slot], err, st, bounded);
+            launch_stage(stage, d_desc + (size_t)slot * n, n, P, d_tail, err, st, bounded);
         }
     };
     // step j of this call runs rotation phase j % 3; a rotation starting at a phase-0 step is one

@@ -387,18 +387,21 @@ struct Stage3Args {
 
 // Work decomposition: blockIdx.x = direction cell (fastest, so that the CTAs resident at a time
 // cover many directions of one spatial tile and the theta/phi neighbours of a cell are read from L2),
-// blockIdx.y = 64 x TY3 tile in (x, y), blockIdx.z = chunk of ZC3 z slices marched by the CTA (the z
-// neighbours of the next slice are the ones just read).
+// blockIdx.y = (2 blockDim.x) x blockDim.y tile in (x, y), blockIdx.z = chunk of ZC3 z slices marched
+// by the CTA (the z neighbours of the next slice are the ones just read).  The tile shape is chosen
+// per grid so that it divides nx and ny where it can (tile_shape3d): a 64-cell row on a 96-cell
+// grid left a quarter of the lanes idle.
 constexpr int ZC3 = 8;
-constexpr int TY3 = 8;    // y rows of a tile (256 threads, 64 registers: 4 blocks per SM)
+constexpr int MAXT3 = 256;  // threads per block at most (64 registers: 4 such blocks per SM)
 
 template <int STAGE>
-__global__ void __launch_bounds__(32 * TY3, 32 / TY3) k_rk3_3d(Stage3Args A) {
+__global__ void __launch_bounds__(MAXT3, 4) k_rk3_3d(Stage3Args A) {
     const Grid3D &g = A.g;
-    int nxt = (g.nx + 63) / 64;
+    const int px = blockDim.x;  // x pairs per tile row
+    int nxt = (g.nx + 2 * px - 1) / (2 * px);
     int dir = blockIdx.x;
-    int ix = 2 * ((blockIdx.y % nxt) * 32 + threadIdx.x);
-    int iy = (blockIdx.y / nxt) * TY3 + threadIdx.y;
+    int ix = 2 * ((blockIdx.y % nxt) * px + threadIdx.x);
+    int iy = (blockIdx.y / nxt) * blockDim.y + threadIdx.y;
     if (ix >= g.nx || iy >= g.ny) return;
     int zend = min((int)(blockIdx.z + 1) * ZC3, g.nz);
     for (int iz = blockIdx.z * ZC3; iz < zend; ++iz) {
@@ -496,6 +499,26 @@ __global__ void __launch_bounds__(32 * TY3, 32 / TY3) k_rk3_3d(Stage3Args A) {
     }
 }
 
+// Thread tile of k_rk3_3d for an nx x ny plane: x pairs per row in {32, 16, 8}, rows in
+// {4, 8, 16, 32}, 128 or 256 threads; the fewest idle lanes (cells of the tiles outside the grid),
+// then 256 threads, then the longer rows (coalescing).
+static dim3 tile_shape3d(int nx, int ny) {
+    int best_px = 32, best_ty = 8;
+    long best_waste = -1;
+    int best_threads = 0;
+    for (int px : {32, 16, 8})
+        for (int ty : {32, 16, 8, 4}) {
+            int threads = px * ty;
+            if (threads != 128 && threads != MAXT3) continue;
+            long w = 2L * px * ((nx + 2 * px - 1) / (2 * px)), h = (long)ty * ((ny + ty - 1) / ty);
+            long waste = w * h - (long)nx * ny;
+            bool better = best_waste < 0 || waste < best_waste ||
+                          (waste == best_waste && threads > best_threads);
+            if (better) { best_waste = waste; best_px = px; best_ty = ty; best_threads = threads; }
+        }
+    return dim3(best_px, best_ty);
+}
+
 cudaError_t solve3d_evolve(Solve3D &sv, int steps, cudaStream_t s) {
     const Grid3D &g = sv.g;
     Stage3Args A;
@@ -510,8 +533,9 @@ cudaError_t solve3d_evolve(Solve3D &sv, int steps, cudaStream_t s) {
     A.eps[1] = 1e-6f;
     A.eps[2] = 1e-6f;
     A.eps[3] = (float)(1e-6 * (h / sv.c_ref) * (h / sv.c_ref));
-    dim3 block(32, TY3);
-    dim3 grid(g.nph * g.nth, ((g.nx + 63) / 64) * ((g.ny + TY3 - 1) / TY3), (g.nz + ZC3 - 1) / ZC3);
+    dim3 block = tile_shape3d(g.nx, g.ny);
+    const int tw = 2 * (int)block.x, th = (int)block.y;
+    dim3 grid(g.nph * g.nth, ((g.nx + tw - 1) / tw) * ((g.ny + th - 1) / th), (g.nz + ZC3 - 1) / ZC3);
     float *U = sv.state[0], *B = sv.state[1], *C = sv.state[2];
     for (int st = 0; st < steps; ++st) {
         A.un = U;

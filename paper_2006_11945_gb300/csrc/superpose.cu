@@ -92,18 +92,27 @@ struct CellData {
     float tau_hi, tau_lo;
 };
 
+// The impact parameter is read from k_beam_fields' unpadded copy A.B, or with PADDED_B straight from
+// the padded state (the same values and differences, for kernels that run without k_beam_fields).
+template <bool PADDED_B = false>
 __device__ CellData load_cell(const SupArgs &A, int k, int iz, int ix) {
     const Grid2D &g = A.g;
     CellData d;
     int64_t o = cidx(g, k, iz, ix);
     int64_t plane = (int64_t)g.nx * g.nz;
     float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
-    d.bx = grad_line(A.B, o, ix, g.nx, 1, ihx);
-    d.bz = grad_line(A.B, o, iz, g.nz, g.nx, ihz);
     int kp = (k + 1) % g.nth, km = (k - 1 + g.nth) % g.nth;
-    d.bt = (A.B[cidx(g, kp, iz, ix)] - A.B[cidx(g, km, iz, ix)]) * 0.5f * idth;
-    const float *Th = A.st + 2 * g.field;
     int64_t p = pidx(g, k, iz, ix);
+    if (PADDED_B) {
+        d.bx = grad_line(A.st, p, ix, g.nx, 1, ihx);
+        d.bz = grad_line(A.st, p, iz, g.nz, g.pitch, ihz);
+        d.bt = (A.st[pidx(g, kp, iz, ix)] - A.st[pidx(g, km, iz, ix)]) * 0.5f * idth;
+    } else {
+        d.bx = grad_line(A.B, o, ix, g.nx, 1, ihx);
+        d.bz = grad_line(A.B, o, iz, g.nz, g.nx, ihz);
+        d.bt = (A.B[cidx(g, kp, iz, ix)] - A.B[cidx(g, km, iz, ix)]) * 0.5f * idth;
+    }
+    const float *Th = A.st + 2 * g.field;
     d.tx = grad_line_angle(Th, p, ix, g.nx, 1, ihx);
     d.tz = grad_line_angle(Th, p, iz, g.nz, g.pitch, ihz);
     d.tt = wrap_angle(Th[pidx(g, kp, iz, ix)] - Th[pidx(g, km, iz, ix)]) * 0.5f * idth;
@@ -240,120 +249,143 @@ __device__ __forceinline__ float phase_mod(float ohi, float olo, float thi, floa
 }
 
 // One line (row if ROW, else column) per thread; up to KC beam centres.
+// Beam data of the centre between cells i and i + 1 of a grid line (the sign change of b there):
+// position, slowness along the line and, per frequency, the complex amplitude and Hessian.
 template <bool ROW>
-__global__ void k_centres(SupArgs A) {
+__device__ void centre_data(const SupArgs &A, const float *as, int k, int line, int i, int64_t slot,
+                            int64_t lines_total) {
+    const Grid2D &g = A.g;
+    float rho_s = A.src[21], c_ref = A.src[22];
+    // sin, cos theta_k from the source block (the float rounding of the double sin, cos of 2 pi k / n)
+    const float sth = A.src[src_sc(g.nth, k)], cth = A.src[src_sc(g.nth, k) + 1];
+    float h = ROW ? (float)g.hx : (float)g.hz;
+    int iz0 = ROW ? line : i, ix0 = ROW ? i : line;
+    int iz1 = ROW ? line : i + 1, ix1 = ROW ? i + 1 : line;
+    int64_t o0 = cidx(g, k, iz0, ix0), o1 = cidx(g, k, iz1, ix1);
+    float b0 = A.B[o0], b1 = A.B[o1];
+    float t = b0 / (b0 - b1);
+    CellData c0 = load_cell(A, k, iz0, ix0), c1 = load_cell(A, k, iz1, ix1);
+    auto L = [t](float a, float b) { return a + t * (b - a); };
+    float bx = L(c0.bx, c1.bx), bz = L(c0.bz, c1.bz), bt = L(c0.bt, c1.bt);
+    float tx = L(c0.tx, c1.tx), tz = L(c0.tz, c1.tz), tt = L(c0.tt, c1.tt);
+    float Vx = L(c0.Vx, c1.Vx), Vz = L(c0.Vz, c1.Vz), td = L(c0.td, c1.td);
+    float pdx = L(c0.pdx, c1.pdx), pdz = L(c0.pdz, c1.pdz), v = L(c0.v, c1.v);
+    float rho = L(c0.rho, c1.rho);
+    float thc = c0.th + t * wrap_angle(c1.th - c0.th);
+    float tau_hi = c0.tau_hi;
+    float tau_lo = c0.tau_lo + t * ((c1.tau_hi - c0.tau_hi) + (c1.tau_lo - c0.tau_lo));
+    // dynamic ray tracing from the label gradients
+    float e[3] = {Vx, Vz, td}, k1[3] = {bx, bz, bt}, k2[3] = {tx, tz, tt}, db[3], dT[3];
+    ray_families(e, k1, k2, db, dT);
+    // sheet of the square root: the continued argument, sampled once more on both cells and
+    // interpolated, against the principal argument of the reference spreading at the centre
+    float al0 = A.alpha[o0], al1 = A.alpha[o1], a0, a1, ac;
+    if (cell_ref_arg(c0.bx, c0.bz, c0.bt, c0.tx, c0.tz, c0.tt, c0.Vx, c0.Vz, c0.td, A.iw0, a0))
+        al0 = lift_branch(al0, a0);
+    if (cell_ref_arg(c1.bx, c1.bz, c1.bt, c1.tx, c1.tz, c1.tt, c1.Vx, c1.Vz, c1.td, A.iw0, a1))
+        al1 = lift_branch(al1, a1);
+    float sigma = 1.f;
+    if (ref_arg(db, dT, Vx, Vz, A.iw0, ac)) {
+        float kk = rintf((L(al0, al1) - ac) * 0.159154943091895335769f);
+        sigma = (((int)kk) & 1) ? -1.f : 1.f;
+    }
+    float ss, cs;
+    sincosf(thc, &ss, &cs);
+    SrcVel sv = source_velocity(as, ss, cs);
+    float pxl = sth / v, pzl = cth / v;
+    float vth = cth * Vx - sth * Vz;
+    float iv2 = 1.f / (v * v);
+    float dpth_x = (cth * v - sth * vth) * iv2, dpth_z = (-sth * v - cth * vth) * iv2;
+    // take-off measure times the row/column blend b_l^2 / |grad b|^2 (bounded where the level
+    // line of b runs along the grid line): |vartheta_theta b_l - vartheta_l b_theta| |b_l| / |grad b|^2
+    float g2 = bx * bx + bz * bz;
+    float wj, pl, pos;
+    if (ROW) {
+        wj = fabsf(tt * bx - tx * bt) * fabsf(bx) / g2;
+        pl = pxl;
+    } else {
+        wj = fabsf(tt * bz - tz * bt) * fabsf(bz) / g2;
+        pl = pzl;
+    }
+    pos = (float)((double)i * h) + t * h;
+    float wreal = g.dth * wj * c_ref * c_ref / (4.f * 3.14159265358979f * sv.v * sv.v);
+    (ROW ? A.rpos : A.cpos)[slot] = pos;
+    (ROW ? A.rp : A.cp)[slot] = pl;
+    for (int w = 0; w < A.n_omega; ++w) {
+        double om = A.omega_dev[w];
+        float omf = (float)om;
+        float kap = 2.f * sv.Vn / (omf * A.w0 * A.w0);
+        cf dx = {db[0], kap * dT[0]}, dz = {db[1], kap * dT[1]}, dth = {db[2], kap * dT[2]};
+        cf pdd = {pdx * dx.re + pdz * dz.re, pdx * dx.im + pdz * dz.im};
+        cf dpx = {pxl * pdd.re + dpth_x * dth.re, pxl * pdd.im + dpth_x * dth.im};
+        cf dpz = {pzl * pdd.re + dpth_z * dth.re, pzl * pdd.im + dpth_z * dth.im};
+        cf J = {dx.re * Vz - dz.re * Vx, dx.im * Vz - dz.im * Vx};
+        cf M;
+        if (ROW) M = cdiv(cf{dpx.re * Vz - pdx * dz.re, dpx.im * Vz - pdx * dz.im}, J);
+        else M = cdiv(cf{-dpz.re * Vx + pdz * dx.re, -dpz.im * Vx + pdz * dx.im}, J);
+        // square root continued along the ray: J = J_b + kappa J_T has the sign of Im J_ref, so
+        // the sheet found for J_ref is this frequency's too
+        cf amp = csqrt_pr(cdiv(cf{rho_s * sv.Vn / rho, 0.f}, J));
+        // coef = i * wreal * sigma * amp
+        cf coef = {-wreal * sigma * amp.im, wreal * sigma * amp.re};
+        float ohi = omf, olo = (float)(om - (double)ohi);
+        float ph = phase_mod(ohi, olo, tau_hi, tau_lo, A.C1, A.C2, A.C3);
+        float sp, cp;
+        sincosf(ph, &sp, &cp);
+        cf E = cmul(coef, cf{cp, sp});
+        // a centre where the level-set Jacobian is singular (no finite beam) carries no weight
+        if (!(isfinite(E.re) && isfinite(E.im) && isfinite(M.re) && isfinite(M.im))) {
+            E = cf{0.f, 0.f};
+            M = cf{0.f, 0.f};
+        }
+        // Im M annihilates V, so Im M_ll >= 0 along a grid line up to discretisation error; the
+        // Gaussian factor uses max(Im M_ll, 0) so that no beam grows away from its centre
+        (ROW ? A.rdat : A.cdat)[(int64_t)w * lines_total + slot] =
+            make_float4(E.re, E.im, M.re, fmaxf(M.im, 0.f));
+    }
+}
+
+// Beam centres of grid lines: one warp per line (k, row or column).  The lanes test 32 neighbouring
+// cell pairs at a time for a sign change of b between flagged cells, a ballot numbers the
+// crossings in line order, and the first KC of them are then computed one per lane (centre_data);
+// more than KC set the overflow flag.  The kept centres and their order are those of a serial scan.
+constexpr int CENTRE_WARPS = 4;
+
+template <bool ROW>
+__global__ void __launch_bounds__(32 * CENTRE_WARPS) k_centres(SupArgs A) {
     const Grid2D &g = A.g;
     __shared__ float as[21];
+    __shared__ int at[CENTRE_WARPS][KC];
     if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
     __syncthreads();
-    int line = blockIdx.x * blockDim.x + threadIdx.x;
-    int nl = ROW ? g.nz : g.nx;
-    int len = ROW ? g.nx : g.nz;
-    int k = blockIdx.y;
-    if (line >= nl) return;
-    int64_t slot0 = ((int64_t)k * nl + line) * KC;
-    int64_t lines_total = (int64_t)g.nth * nl * KC;
-    float rho_s = A.src[21], c_ref = A.src[22];
-    float sth, cth;
-    {
-        double th = 2.0 * M_PI * k / g.nth;
-        sth = (float)sin(th);
-        cth = (float)cos(th);
-    }
-    float h = ROW ? (float)g.hx : (float)g.hz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nl = ROW ? g.nz : g.nx;
+    const int len = ROW ? g.nx : g.nz;
+    const int line = blockIdx.x * CENTRE_WARPS + warp;
+    const int k = blockIdx.y;
+    if (line >= nl) return;  // the whole warp
     int cnt = 0;
-    for (int i = 0; i + 1 < len; ++i) {
-        int iz0 = ROW ? line : i, ix0 = ROW ? i : line;
-        int iz1 = ROW ? line : i + 1, ix1 = ROW ? i + 1 : line;
-        int64_t o0 = cidx(g, k, iz0, ix0), o1 = cidx(g, k, iz1, ix1);
-        if (!(A.FL[o0] && A.FL[o1])) continue;
-        float b0 = A.B[o0], b1 = A.B[o1];
-        if ((b0 >= 0.f) == (b1 >= 0.f)) continue;
-        if (cnt >= KC) { atomicOr(A.err, DeviceErrors::OVERFLOW); break; }
-        float t = b0 / (b0 - b1);
-        CellData c0 = load_cell(A, k, iz0, ix0), c1 = load_cell(A, k, iz1, ix1);
-        auto L = [t](float a, float b) { return a + t * (b - a); };
-        float bx = L(c0.bx, c1.bx), bz = L(c0.bz, c1.bz), bt = L(c0.bt, c1.bt);
-        float tx = L(c0.tx, c1.tx), tz = L(c0.tz, c1.tz), tt = L(c0.tt, c1.tt);
-        float Vx = L(c0.Vx, c1.Vx), Vz = L(c0.Vz, c1.Vz), td = L(c0.td, c1.td);
-        float pdx = L(c0.pdx, c1.pdx), pdz = L(c0.pdz, c1.pdz), v = L(c0.v, c1.v);
-        float rho = L(c0.rho, c1.rho);
-        float thc = c0.th + t * wrap_angle(c1.th - c0.th);
-        float tau_hi = c0.tau_hi;
-        float tau_lo = c0.tau_lo + t * ((c1.tau_hi - c0.tau_hi) + (c1.tau_lo - c0.tau_lo));
-        // dynamic ray tracing from the label gradients
-        float e[3] = {Vx, Vz, td}, k1[3] = {bx, bz, bt}, k2[3] = {tx, tz, tt}, db[3], dT[3];
-        ray_families(e, k1, k2, db, dT);
-        // sheet of the square root: the continued argument, sampled once more on both cells and
-        // interpolated, against the principal argument of the reference spreading at the centre
-        float al0 = A.alpha[o0], al1 = A.alpha[o1], a0, a1, ac;
-        if (cell_ref_arg(c0.bx, c0.bz, c0.bt, c0.tx, c0.tz, c0.tt, c0.Vx, c0.Vz, c0.td, A.iw0, a0))
-            al0 = lift_branch(al0, a0);
-        if (cell_ref_arg(c1.bx, c1.bz, c1.bt, c1.tx, c1.tz, c1.tt, c1.Vx, c1.Vz, c1.td, A.iw0, a1))
-            al1 = lift_branch(al1, a1);
-        float sigma = 1.f;
-        if (ref_arg(db, dT, Vx, Vz, A.iw0, ac)) {
-            float kk = rintf((L(al0, al1) - ac) * 0.159154943091895335769f);
-            sigma = (((int)kk) & 1) ? -1.f : 1.f;
+    for (int base = 0; base + 1 < len; base += 32) {
+        const int i = base + lane;
+        bool cross = false;
+        if (i + 1 < len) {
+            int iz0 = ROW ? line : i, ix0 = ROW ? i : line;
+            int iz1 = ROW ? line : i + 1, ix1 = ROW ? i + 1 : line;
+            int64_t o0 = cidx(g, k, iz0, ix0), o1 = cidx(g, k, iz1, ix1);
+            cross = A.FL[o0] && A.FL[o1] && ((A.B[o0] >= 0.f) != (A.B[o1] >= 0.f));
         }
-        float ss, cs;
-        sincosf(thc, &ss, &cs);
-        SrcVel sv = source_velocity(as, ss, cs);
-        float pxl = sth / v, pzl = cth / v;
-        float vth = cth * Vx - sth * Vz;
-        float iv2 = 1.f / (v * v);
-        float dpth_x = (cth * v - sth * vth) * iv2, dpth_z = (-sth * v - cth * vth) * iv2;
-        // take-off measure times the row/column blend b_l^2 / |grad b|^2 (bounded where the level
-        // line of b runs along the grid line): |vartheta_theta b_l - vartheta_l b_theta| |b_l| / |grad b|^2
-        float g2 = bx * bx + bz * bz;
-        float wj, pl, pos;
-        if (ROW) {
-            wj = fabsf(tt * bx - tx * bt) * fabsf(bx) / g2;
-            pl = pxl;
-        } else {
-            wj = fabsf(tt * bz - tz * bt) * fabsf(bz) / g2;
-            pl = pzl;
-        }
-        pos = (float)((double)i * h) + t * h;
-        float wreal = g.dth * wj * c_ref * c_ref / (4.f * 3.14159265358979f * sv.v * sv.v);
-        int64_t slot = slot0 + cnt;
-        (ROW ? A.rpos : A.cpos)[slot] = pos;
-        (ROW ? A.rp : A.cp)[slot] = pl;
-        for (int w = 0; w < A.n_omega; ++w) {
-            double om = A.omega_dev[w];
-            float omf = (float)om;
-            float kap = 2.f * sv.Vn / (omf * A.w0 * A.w0);
-            cf dx = {db[0], kap * dT[0]}, dz = {db[1], kap * dT[1]}, dth = {db[2], kap * dT[2]};
-            cf pdd = {pdx * dx.re + pdz * dz.re, pdx * dx.im + pdz * dz.im};
-            cf dpx = {pxl * pdd.re + dpth_x * dth.re, pxl * pdd.im + dpth_x * dth.im};
-            cf dpz = {pzl * pdd.re + dpth_z * dth.re, pzl * pdd.im + dpth_z * dth.im};
-            cf J = {dx.re * Vz - dz.re * Vx, dx.im * Vz - dz.im * Vx};
-            cf M;
-            if (ROW) M = cdiv(cf{dpx.re * Vz - pdx * dz.re, dpx.im * Vz - pdx * dz.im}, J);
-            else M = cdiv(cf{-dpz.re * Vx + pdz * dx.re, -dpz.im * Vx + pdz * dx.im}, J);
-            // square root continued along the ray: J = J_b + kappa J_T has the sign of Im J_ref, so
-            // the sheet found for J_ref is this frequency's too
-            cf amp = csqrt_pr(cdiv(cf{rho_s * sv.Vn / rho, 0.f}, J));
-            // coef = i * wreal * sigma * amp
-            cf coef = {-wreal * sigma * amp.im, wreal * sigma * amp.re};
-            float ohi = omf, olo = (float)(om - (double)ohi);
-            float ph = phase_mod(ohi, olo, tau_hi, tau_lo, A.C1, A.C2, A.C3);
-            float sp, cp;
-            sincosf(ph, &sp, &cp);
-            cf E = cmul(coef, cf{cp, sp});
-            // a centre where the level-set Jacobian is singular (no finite beam) carries no weight
-            if (!(isfinite(E.re) && isfinite(E.im) && isfinite(M.re) && isfinite(M.im))) {
-                E = cf{0.f, 0.f};
-                M = cf{0.f, 0.f};
-            }
-            // Im M annihilates V, so Im M_ll >= 0 along a grid line up to discretisation error; the
-            // Gaussian factor uses max(Im M_ll, 0) so that no beam grows away from its centre
-            (ROW ? A.rdat : A.cdat)[(int64_t)w * lines_total + slot] =
-                make_float4(E.re, E.im, M.re, fmaxf(M.im, 0.f));
-        }
-        ++cnt;
+        const unsigned m = __ballot_sync(0xffffffffu, cross);
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (cross && pos < KC) at[warp][pos] = i;
+        cnt += __popc(m);
     }
-    (ROW ? A.rcnt : A.ccnt)[(int64_t)k * nl + line] = cnt;
+    __syncwarp();
+    if (cnt > KC && lane == 0) atomicOr(A.err, DeviceErrors::OVERFLOW);
+    const int n = cnt < KC ? cnt : KC;
+    const int64_t slot0 = ((int64_t)k * nl + line) * KC;
+    const int64_t lines_total = (int64_t)g.nth * nl * KC;
+    if (lane < n) centre_data<ROW>(A, as, k, line, at[warp][lane], slot0 + lane, lines_total);
+    if (lane == 0) (ROW ? A.rcnt : A.ccnt)[(int64_t)k * nl + line] = n;
 }
 
 // One beam's term at a receiver offset d along its grid line (d in m), accumulated into (re, im).
@@ -422,15 +454,22 @@ __global__ void k_sum(SupArgs A, float2 *u) {
 // vanish at a small |db|, leaving an undamped term whose phase hangs on the labels' last digits).
 // Amplitude sqrt(rho0 |V0| / (rho_s |V_s(vartheta)| db)) (principal root: rays without a
 // caustic), weight i c0^2 / (4 pi v0^2) dtheta, and the sum rescaled by
-// rho_s c_s^2 / (rho0 c0^2) to the source side's normalisation (reciprocity).  Lanes split the
-// angles of a receiver as in k_sum.
-__global__ void k_sum_receiver(SupArgs A, const float *__restrict__ med_a, float2 *u) {
+// rho_s c_s^2 / (rho0 c0^2) to the source side's normalisation (reciprocity).
+// Layout: a block serves RX_W neighbouring receivers of one row (one per lane, so every gather of a
+// warp is one coalesced row segment) and its RX_WARPS warps split the angles (warp w takes theta_k
+// with k = w mod RX_WARPS); each cell is read once and its terms for up to RX_MAXW frequencies are
+// accumulated in registers; the warps' partial sums are added in shared memory.
+constexpr int RX_W = 32, RX_WARPS = 8, RX_MAXW = 8;
+
+__global__ void __launch_bounds__(RX_W * RX_WARPS) k_sum_receiver(SupArgs A, const float *__restrict__ med_a,
+                                                                   float2 *u) {
     const Grid2D &g = A.g;
     __shared__ float as[21];
+    __shared__ float ohs[RX_MAXW], ols[RX_MAXW];
+    __shared__ float2 part[RX_WARPS][RX_MAXW][RX_W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, t = lane % SUM_LANES;
-    const int ix = blockIdx.x * (blockDim.x / SUM_LANES) + threadIdx.x / SUM_LANES;
+    const int ix = blockIdx.x * RX_W + lane;
     const int iz = blockIdx.y;
     const bool rx = ix < g.nx;
     const int ixc = rx ? ix : g.nx - 1;
@@ -441,54 +480,79 @@ __global__ void k_sum_receiver(SupArgs A, const float *__restrict__ med_a, float
     const float c0 = source_velocity(a0, 0.f, 1.f).v;  // qP phase velocity along +z at x0
     const float rho0 = A.rho[node], rho_s = A.src[21], c_s = A.src[22];
     const float four_pi = 12.5663706143591729f;
-    for (int w = 0; w < A.n_omega; ++w) {
-        double om = A.omega_dev[w];
-        float omf = (float)om, ohi = omf, olo = (float)(om - (double)ohi);
-        float kap = -2.f / (omf * A.w0 * A.w0);  // kappa0 / (i |V0|)
-        float are = 0.f, aim = 0.f;
-        for (int k = t; k < g.nth; k += SUM_LANES) {
-            int64_t o = cidx(g, k, iz, ixc);
-            if (!A.FL[o]) continue;
-            CellData d = load_cell(A, k, iz, ixc);
-            float b = A.B[o];
-            float V0 = hypotf(d.Vx, d.Vz), gx = d.Vx / V0, gz = d.Vz / V0;
-            float b_perp = d.bx * gz - d.bz * gx, t_perp = d.tx * gz - d.tz * gx;
+    for (int w0 = 0; w0 < A.n_omega; w0 += RX_MAXW) {
+        const int nw = min(RX_MAXW, A.n_omega - w0);
+        __syncthreads();  // as[] loaded; the previous pass's partial sums consumed
+        if (threadIdx.x < nw) {  // omega as a double-float pair (hi, lo)
+            double om = A.omega_dev[w0 + threadIdx.x];
+            float hi = (float)om;
+            ohs[threadIdx.x] = hi;
+            ols[threadIdx.x] = (float)(om - (double)hi);
+        }
+        __syncthreads();
+        float are[RX_MAXW], aim[RX_MAXW];
+#pragma unroll
+        for (int w = 0; w < RX_MAXW; ++w) are[w] = aim[w] = 0.f;
+        for (int k = warp; k < g.nth; k += RX_WARPS) {
+            // rays that carry source labels and have left the frozen manifold
+            const int64_t p = pidx(g, k, iz, ixc);
+            if (!(A.st[g.field + p] > 0.5f) || A.frozen[cidx(g, k, iz, ixc)]) continue;
+            CellData d = load_cell<true>(A, k, iz, ixc);
+            const float b = A.st[p];
+            const float V0 = hypotf(d.Vx, d.Vz), gx = d.Vx / V0, gz = d.Vz / V0;
+            const float b_perp = d.bx * gz - d.bz * gx, t_perp = d.tx * gz - d.tz * gx;
             float sth, cth;
             sincosf(d.th, &sth, &cth);
-            SrcVel sv = source_velocity(as, sth, cth);
-            float vs_t = sv.Vx * cth - sv.Vz * sth;
-            float iv2 = 1.f / (sv.v * sv.v);
-            float dpx = (cth * sv.v - sth * vs_t) * iv2, dpz = (-sth * sv.v - cth * vs_t) * iv2;
-            float dp_perp = (dpx * sv.Vz - dpz * sv.Vx) / sv.Vn;
+            const SrcVel sv = source_velocity(as, sth, cth);
+            const float vs_t = sv.Vx * cth - sv.Vz * sth;
+            const float iv2 = 1.f / (sv.v * sv.v);
+            const float dpx = (cth * sv.v - sth * vs_t) * iv2, dpz = (-sth * sv.v - cth * vs_t) * iv2;
+            const float dp_perp = (dpx * sv.Vz - dpz * sv.Vx) / sv.Vn;
             // receiver medium at the cell's own angle: dp/dtheta . (g_z, -g_x) fixes Im M through
             // the beam's Wronskian (the label Jacobian keeps it only up to discretisation error)
             const float s0 = A.src[src_sc(g.nth, k)], c0k = A.src[src_sc(g.nth, k) + 1];
-            float v0_t = d.Vx * c0k - d.Vz * s0, iv02 = 1.f / (d.v * d.v);
-            float dp0x = (c0k * d.v - s0 * v0_t) * iv02, dp0z = (-s0 * d.v - c0k * v0_t) * iv02;
-            float dp0_perp = dp0x * gz - dp0z * gx;
-            cf db = {b_perp, kap * V0 * d.bt}, dth = {t_perp, kap * V0 * d.tt};
-            cf M = cdiv(dth, db);
-            M = {-dp_perp * M.re, -kap * V0 * dp0_perp / (db.re * db.re + db.im * db.im)};
-            cf amp = csqrt_pr(cdiv(cf{rho0 * V0 / (rho_s * sv.Vn), 0.f}, db));
-            float wgt = g.dth * c0 * c0 / (four_pi * d.v * d.v);
-            float ph = phase_mod(ohi, olo, d.tau_hi, d.tau_lo, A.C1, A.C2, A.C3) + 0.5f * omf * M.re * b * b;
-            float dec = -0.5f * omf * M.im * b * b;
-            if (!(dec > -60.f)) continue;  // far outside the beam (or not finite)
-            float mag = wgt * __expf(dec), sp, cp;
-            sincosf(ph, &sp, &cp);
-            // i * mag * amp * exp(i ph)
-            cf e = cmul(amp, cf{cp, sp});
-            if (!(isfinite(e.re) && isfinite(e.im))) continue;
-            are -= mag * e.im;
-            aim += mag * e.re;
+            const float v0_t = d.Vx * c0k - d.Vz * s0, iv02 = 1.f / (d.v * d.v);
+            const float dp0x = (c0k * d.v - s0 * v0_t) * iv02, dp0z = (-s0 * d.v - c0k * v0_t) * iv02;
+            const float dp0_perp = dp0x * gz - dp0z * gx;
+            const float pre = rho0 * V0 / (rho_s * sv.Vn);
+            const float wgt = g.dth * c0 * c0 / (four_pi * d.v * d.v);
+            const float hb2 = 0.5f * b * b;
+#pragma unroll
+            for (int w = 0; w < RX_MAXW; ++w) {
+                if (w >= nw) break;
+                const float ohi = ohs[w], olo = ols[w];
+                const float kap = -2.f / (ohi * A.w0 * A.w0);  // kappa0 / (i |V0|)
+                const cf db = {b_perp, kap * V0 * d.bt}, dth = {t_perp, kap * V0 * d.tt};
+                const float Mre = -dp_perp * cdiv(dth, db).re;
+                const float Mim = -kap * V0 * dp0_perp / (db.re * db.re + db.im * db.im);
+                const float dec = -ohi * Mim * hb2;
+                if (!(dec > -60.f)) continue;  // far outside the beam (or not finite)
+                const cf amp = csqrt_pr(cdiv(cf{pre, 0.f}, db));
+                const float ph = phase_mod(ohi, olo, d.tau_hi, d.tau_lo, A.C1, A.C2, A.C3) + ohi * Mre * hb2;
+                float sp, cp;
+                sincosf(ph, &sp, &cp);
+                const float mag = wgt * __expf(dec);
+                // i * mag * amp * exp(i ph)
+                const cf e = cmul(amp, cf{cp, sp});
+                if (!(isfinite(e.re) && isfinite(e.im))) continue;
+                are[w] -= mag * e.im;
+                aim[w] += mag * e.re;
+            }
         }
 #pragma unroll
-        for (int m = SUM_LANES / 2; m > 0; m >>= 1) {
-            are += __shfl_xor_sync(0xffffffffu, are, m);
-            aim += __shfl_xor_sync(0xffffffffu, aim, m);
+        for (int w = 0; w < RX_MAXW; ++w) part[warp][w][lane] = make_float2(are[w], aim[w]);
+        __syncthreads();
+        // warp w' adds the RX_WARPS partial sums of frequency w' (and w' + RX_WARPS, ...)
+        const float sc = rho_s * c_s * c_s / (rho0 * c0 * c0);
+        for (int w = warp; w < nw; w += RX_WARPS) {
+            float sre = 0.f, sim = 0.f;
+#pragma unroll
+            for (int q = 0; q < RX_WARPS; ++q) {
+                sre += part[q][w][lane].x;
+                sim += part[q][w][lane].y;
+            }
+            if (rx) u[((int64_t)(w0 + w) * g.nz + iz) * g.nx + ix] = make_float2(sc * sre, sc * sim);
         }
-        float sc = rho_s * c_s * c_s / (rho0 * c0 * c0);
-        if (rx && t == 0) u[((int64_t)w * g.nz + iz) * g.nx + ix] = make_float2(sc * are, sc * aim);
     }
 }
 
@@ -591,8 +655,8 @@ cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, doubl
     dim3 gb((g.nx + 127) / 128, g.nz, g.nth);
     k_beam_fields<<<gb, 128, 0, s>>>(A);
     if (u_dev) {
-        k_centres<true><<<dim3((g.nz + 63) / 64, g.nth), 64, 0, s>>>(A);
-        k_centres<false><<<dim3((g.nx + 63) / 64, g.nth), 64, 0, s>>>(A);
+        k_centres<true><<<dim3((g.nz + CENTRE_WARPS - 1) / CENTRE_WARPS, g.nth), 32 * CENTRE_WARPS, 0, s>>>(A);
+        k_centres<false><<<dim3((g.nx + CENTRE_WARPS - 1) / CENTRE_WARPS, g.nth), 32 * CENTRE_WARPS, 0, s>>>(A);
         k_sum<<<dim3((g.nx + 256 / SUM_LANES - 1) / (256 / SUM_LANES), g.nz), 256, 0, s>>>(A, u_dev);
     }
     if (count_dev || T_dev || A_dev)
@@ -605,9 +669,7 @@ cudaError_t launch_superpose_receiver(Solve &sv, float2 *u_dev, unsigned *d_err,
     cudaError_t e = superpose_args(sv, d_err, s, A);
     if (e != cudaSuccess) return e;
     const Grid2D &g = sv.g;
-    dim3 gb((g.nx + 127) / 128, g.nz, g.nth);
-    k_beam_fields<<<gb, 128, 0, s>>>(A);
-    k_sum_receiver<<<dim3((g.nx + 256 / SUM_LANES - 1) / (256 / SUM_LANES), g.nz), 256, 0, s>>>(A, sv.m->a, u_dev);
+    k_sum_receiver<<<dim3((g.nx + RX_W - 1) / RX_W, g.nz), RX_W * RX_WARPS, 0, s>>>(A, sv.m->a, u_dev);
     return cudaGetLastError();
 }
 
