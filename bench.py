@@ -46,8 +46,8 @@ ALGO_BYTES_PER_CELL_UPDATE = 52.0
 # (stage 1: 917 MB, stages 2 and 3: 1285 and 1284 MB per 16.8 M cells), with the SHA-256 of the
 # kernel's device source it was taken on; traffic grows with the cells a launch processes, so the
 # figure is scaled to the timed workload.  Reported as null once the device source differs.
-STENCIL_TRAFFIC = {'bytes_per_cell_launch': (54.75 + 78.44 + 78.58) / 3.0,
-                   'device_source_sha256': '43f3a363c8d7ceedc11ad8b8a6f391e386d072b408408a702fb643433420d06e'}
+STENCIL_TRAFFIC = {'bytes_per_cell_launch': (55.04 + 77.42 + 77.34) / 3.0,
+                   'device_source_sha256': '327db6ccac3f8c6d4fba2645ac44b331cd09c4c937f6076f8595bc09c97e0faa'}
 
 
 def stencil_traffic_per_launch(cells):
@@ -60,10 +60,10 @@ def stencil_traffic_per_launch(cells):
 
 
 # Instruction issue of k_rk3_tma per cell and stage launch (ncu, thread-level instructions of the
-# stage-2 launch on the 256^2 x 256 TTI case: 329.5, of which FP32 182.3 and integer 66.0), and
+# stage-2 launch on the 256^2 x 256 TTI case: 317.3, of which FP32 182.1 and integer 60.4), and
 # GB300's issue ceiling: 4 schedulers per SM issue one warp instruction (32 thread instructions)
 # per cycle.
-STENCIL_THREAD_INST_PER_CELL_STAGE = 329.5
+STENCIL_THREAD_INST_PER_CELL_STAGE = 317.3
 
 
 def issue_ceiling_thread_inst_per_s(sm_mhz):

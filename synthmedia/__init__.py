@@ -145,6 +145,15 @@ def _gaussian_filter(a, sigma_cells):
     return gaussian_filter(a, sigma=sigma_cells, mode='reflect')
 
 
+def _smooth_uniform(rng, n, sigma_cells, lo, hi):
+    """An n x n smooth random field with values spread uniformly over [lo, hi]: white noise filtered
+    by a Gaussian, standardised, and mapped through the standard normal distribution function."""
+    from scipy.special import ndtr
+    f = _gaussian_filter(rng.standard_normal((n, n)), sigma_cells)
+    f = (f - f.mean()) / f.std()
+    return lo + (hi - lo) * ndtr(f)
+
+
 @dataclass
 class Problem2D:
     """One 2-D solve request: medium on an nz x nx node grid plus the source description."""
@@ -236,9 +245,11 @@ def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 
     """2-D heterogeneous TTI medium.
 
     Vp0 = (2000 + 1.0 z) (1 + 0.15 G1 - 0.15 G2), G_k Gaussians of sigma 300 m centred uniformly in
-    the middle 60 % of the domain; Vs0 = Vp0/1.8; epsilon ~ U[0, 0.25] and delta ~ U[-0.05, 0.15]
-    drawn once for the medium; tilt = white noise filtered by a Gaussian of sigma 200 m, scaled to a
-    maximum of 30 deg; Gardner density.  ``length`` (m) fixes the physical extent so reduced grids
+    the middle 60 % of the domain; Vs0 = Vp0/1.8; epsilon and delta smooth fields with uniform
+    marginals on [0, 0.25] and [-0.05, 0.15]: white noise filtered by a Gaussian of sigma 300 m,
+    standardised and mapped through the normal distribution function onto the interval; tilt =
+    white noise filtered by a Gaussian of sigma 200 m, scaled to a maximum of 30 deg; Gardner
+    density.  ``length`` (m) fixes the physical extent so reduced grids
     (coarser h) describe the same medium; default n*h.  Source at the centre node.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -252,11 +263,15 @@ def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 
     g = [np.exp(-((X - cx) ** 2 + (Z - cz) ** 2) / (2 * sig ** 2)) for cx, cz in centres]
     vp0 = (2000.0 + 1.0 * Z) * (1.0 + 0.15 * g[0] - 0.15 * g[1])
     vs0 = vp0 / 1.8
-    eps = rng.uniform(0.0, 0.25)
-    delta = rng.uniform(-0.05, 0.15)
+    # two uniform draws that once set constant epsilon and delta: kept, so that the tilt field and
+    # the velocity anomalies are those of that earlier form of the medium
+    rng.uniform(0.0, 0.25)
+    rng.uniform(-0.05, 0.15)
     noise = rng.standard_normal((n, n))
     tilt = _gaussian_filter(noise, 200.0 / h)
     tilt = tilt / np.max(np.abs(tilt)) * math.radians(30.0)
+    eps = _smooth_uniform(rng, n, 300.0 / h, 0.0, 0.25)
+    delta = _smooth_uniform(rng, n, 300.0 / h, -0.05, 0.15)
     rho = gardner_density(vp0)
     C = thomsen_vti_voigt(vp0, vs0, eps, delta, rho)
     C = rotate_voigt_about_y(C, tilt)
@@ -267,8 +282,8 @@ def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 
     if beam_width is None:
         beam_width = 50.0
     return Problem2D('tti_heterogeneous', n, n, h, h, c21, r, xs, n_theta, list(freqs), beam_width,
-                     steps, cfl, meta=dict(seed=seed, eps=eps, delta=delta, centres=centres.tolist(),
-                                           length=L))
+                     steps, cfl, meta=dict(seed=seed, eps_mean=float(eps.mean()), delta_mean=float(delta.mean()),
+                                           centres=centres.tolist(), length=L))
 
 
 def tti_default_steps(n, h):
