@@ -314,6 +314,7 @@ def run_egb(args):
             'tri96': measure_3d(p3, p3.steps, 1, 1, warmup_steps=3),
             'batch': measure_batch_waves(synthmedia.batched_instances(count=args.batch_count),
                                          args.evolve_steps or 10, 1, 1),
+            'batch_small': measure_batch_small(),
             'reductions': measure_receiver(p),
             'serve': measure_serve(args.serve_seconds, 1.0, args.serve_chunk,
                                    args.serve_wall if args.serve_wall is not None else 60.0,
@@ -522,6 +523,43 @@ def run_batch(args):
         'clocks': clk.summary(),
     }))
     ctx.close()
+
+
+def measure_batch_small(steps=60, K=3):
+    """Batching where it pays: small instances advanced by one egb_evolve_batch call against one
+    egb_evolve per instance, both timed with CUDA events on the context stream (K calls after one
+    untimed).  Two sets: 32 copies of the 64^2 x 64 VTI instance (the small class of the serving
+    stream) and 64 instances of the uneven recipe scaled by 1/8 (72^2-120^2 grids, 20-62 angles)."""
+    import torch
+    import paper_2006_11945_gb300 as egb
+    sets = {'vti64x32': [synthmedia.vti_homogeneous(n=64, n_theta=64, steps=steps) for _ in range(32)],
+            'uneven_1_8x64': synthmedia.batched_instances(count=64, size_scale=0.125)}
+    out = {}
+    for name, ps in sets.items():
+        stream = torch.cuda.Stream()
+        with egb.Context(0, stream.cuda_stream) as ctx:
+            ids = [ctx.source_2d(ctx.medium_2d(p), p) for p in ps]
+            egb.egb_sync(ctx.h)
+            cells = sum(p.nx * p.nz * p.n_theta for p in ps)
+
+            def timed(fn):
+                fn()
+                egb.egb_sync(ctx.h)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                for _ in range(K):
+                    fn()
+                with torch.cuda.stream(stream):
+                    e1.record(stream)
+                egb.egb_sync(ctx.h)
+                return e0.elapsed_time(e1) / K
+            cfl = ps[0].cfl
+            b = timed(lambda: egb.egb_evolve_batch(ctx.h, ids, [steps] * len(ids), cfl))
+            o = timed(lambda: [egb.egb_evolve(ctx.h, i, steps, cfl) for i in ids])
+        out[name] = {'instances': len(ps), 'cells': cells, 'steps': steps, 'batched_ms': b, 'one_by_one_ms': o,
+                     'speedup': o / b, 'batched_cell_updates_per_s': cells * steps / (b / 1e3)}
+    return out
 
 
 def measure_batch_waves(ps, S, K, W):

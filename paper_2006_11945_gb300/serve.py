@@ -152,6 +152,7 @@ class ServeStats:
     completed: List[Request] = field(default_factory=list)
     cancelled: List[Request] = field(default_factory=list)
     unfinished: List[Request] = field(default_factory=list)   # on the device when wall_limit hit
+    not_admitted: List[Request] = field(default_factory=list)  # still queued when admission closed
     refused_admissions: int = 0
     chunks: int = 0
     work: float = 0.0       # cell-updates advanced on the device (finished or not)
@@ -163,7 +164,7 @@ class ServeStats:
         cells = sum(r.problem.cells * r.problem.steps for r in self.completed)
         return {
             'offered': offered, 'completed': len(self.completed), 'cancelled': len(self.cancelled),
-            'unfinished': len(self.unfinished),
+            'unfinished': len(self.unfinished), 'not_admitted': len(self.not_admitted),
             'solves_per_s': len(self.completed) / self.wall if self.wall > 0 else 0.0,
             'cell_updates_per_s': cells / self.wall if self.wall > 0 else 0.0,
             'device_cell_updates_per_s': self.work / self.wall if self.wall > 0 else 0.0,
@@ -213,11 +214,15 @@ def serve(requests: List[Request], backend, chunk_steps: int = 30, cfl: float = 
                 backend.cancel(r)
                 stats.unfinished.append(r)
             active = []
+            stats.not_admitted.extend(waiting)
+            stats.not_admitted.extend(pending)
             break
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
         admitting = time_limit is None or now < time_limit
         if not admitting:
+            stats.not_admitted.extend(waiting)
+            stats.not_admitted.extend(pending)
             pending.clear()
             waiting.clear()
         # cancellations: waiting requests are dropped, solves on the device released

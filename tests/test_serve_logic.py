@@ -98,6 +98,10 @@ def test_time_limit_stops_admission():
     be = FakeBackend(budget_cells=10 ** 9, clock=clock)
     st = serve(reqs, be, chunk_steps=10, clock=clock, time_limit=0.2)
     assert sorted(r.rid for r in st.completed) == [0, 1]
+    # the requests still queued when admission closed are counted, so every offered one is accounted for
+    assert sorted(r.rid for r in st.not_admitted) == [2, 3, 4]
+    s = st.summary(5)
+    assert s['completed'] + s['cancelled'] + s['unfinished'] + s['not_admitted'] == 5
 
 
 def test_request_cancelled_between_chunks_is_released_and_frees_its_memory():
@@ -144,7 +148,7 @@ def test_wall_limit_releases_unfinished_requests():
     be = FakeBackend(budget_cells=10 ** 9, clock=clock)
     st = serve(reqs, be, chunk_steps=10, clock=clock, wall_limit=0.05)
     assert not st.completed and sorted(r.rid for r in st.unfinished) == [0, 1, 2]
-    assert be.used == 0 and st.summary(3)['unfinished'] == 3
+    assert be.used == 0 and st.summary(3)['unfinished'] == 3 and not st.not_admitted
 
 
 def test_work_budgeted_chunks_finish_small_requests_first():
