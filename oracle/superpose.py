@@ -137,11 +137,27 @@ def track_branch(S, lab, alpha=None):
     return lift_branch(alpha, a)
 
 
+# The last beam_fields result with the objects it was computed from (held, so that their ids stay
+# theirs): the label arrays are treated as immutable, so a later call on the same setup and the same
+# label arrays returns it instead of recomputing (the per-cell eigen-solves dominate a beam sum).
+_fields_memo = {'key': None, 'F': None}
+
+
 def beam_fields(S, lab):
     """Frequency-independent per-cell quantities of the superposition (all float64)."""
+    key = (S, lab) + tuple(lab.get(k) for k in ('b', 'q', 'Th', 'tau', 'alpha'))
+    old = _fields_memo['key']
+    if old is not None and len(old) == len(key) and all(a is c for a, c in zip(old, key)):
+        return _fields_memo['F']
+    F = _beam_fields(S, lab)
+    _fields_memo['key'], _fields_memo['F'] = key, F
+    return F
+
+
+def _beam_fields(S, lab):
     b, q, Th, tau = lab['b'], lab['q'], lab['Th'], lab['tau']
-    vs, _, Vsn, _ = _ch.source_quantities(S.a_s, Th)
-    F = dict(b=b, tau=tau, vs=vs, Vsn=Vsn, Th=Th,
+    vs, Vs, Vsn, gs = _ch.source_quantities(S.a_s, Th)
+    F = dict(b=b, tau=tau, vs=vs, Vs=Vs, Vsn=Vsn, gs=gs, Th=Th,
              # rays whose labels came from the source manifold and that have left it
              flag=(q > 0.5) & ~S.frozen)
     F.update(_label_gradients(S, b, Th))
@@ -327,16 +343,17 @@ def green_receiver(S, lab, omegas, beam_width):
     medium), and the sum, rho0 c0^2 times the Green's function, is rescaled by
     rho_s c_s^2 / (rho0 c0^2) to the source side's normalisation.
     """
-    b, q, Th, tau = lab['b'], lab['q'], lab['Th'], lab['tau']
-    G = _label_gradients(S, b, Th)
-    flag = (q > 0.5) & ~S.frozen
+    # the label gradients, the source flag and the source medium at vartheta are those of the
+    # source-side sum (beam_fields)
+    G = beam_fields(S, lab)
+    b, Th, tau, flag = G['b'], G['Th'], G['tau'], G['flag']
     Vx, Vz, v0 = S.vel['Vx'], S.vel['Vz'], S.vel['v']
     V0 = np.hypot(Vx, Vz)
     gx, gz = Vx / V0, Vz / V0
     b_perp = G['bx'] * gz - G['bz'] * gx
     t_perp = G['Tx'] * gz - G['Tz'] * gx
     # source medium at the closest approach: slowness derivative along vartheta, |V_s|
-    vs, Vs, Vsn, gs = _ch.source_quantities(S.a_s, Th)
+    vs, Vs, Vsn, gs = G['vs'], G['Vs'], G['Vsn'], G['gs']
     n = np.stack([np.sin(Th), np.cos(Th)], -1)
     n_t = np.stack([np.cos(Th), -np.sin(Th)], -1)
     vs_t = np.einsum('...i,...i->...', Vs, n_t)

@@ -20,8 +20,8 @@ from oracle import liouville as L
 from oracle import superpose as SP
 
 
-def _exact_setup(problem):
-    S = L.Setup(problem)
+def _exact_setup(problem, vel=None):
+    S = L.Setup(problem, vel=vel)
     x = np.arange(S.nx) * S.hx - S.xs[0]
     z = np.arange(S.nz) * S.hz - S.xs[1]
     Z, X = np.meshgrid(z, x, indexing='ij')
@@ -120,18 +120,20 @@ def test_heterogeneous_wavefield_is_bounded():
 
 # ---- receiver-side (reciprocal) reduction of the same labels (Eq. 34 read through reciprocity) ----
 
-def _wide_tube(p, R_sigma):
+def _wide_tube(p, R_sigma, vel=None):
+    """The same medium with a source-ray tube of radius R_sigma (vel: its velocity fields, when
+    already computed, which do not depend on the tube)."""
     import dataclasses
-    return _exact_setup(dataclasses.replace(p, R_sigma=R_sigma))
+    return _exact_setup(dataclasses.replace(p, R_sigma=R_sigma), vel=vel)
 
 
 @pytest.fixture(scope='module')
-def iso_wide():
+def iso_wide(iso):
     """The isotropic medium with a 400 m source-ray tube: the receiver-side beams reach x_s about
     w(r) = w0 sqrt(1 + (2 r / (k w0^2))^2) wide (143 m at 640 m, 60 Hz, w0 = 100 m) and need the
     labels of rays up to about 2 w(r) from the source."""
-    p = synthmedia.isotropic_homogeneous(n=128, h=10.0, n_theta=384, freqs=[60.0])
-    return (p,) + _wide_tube(p, 400.0)
+    p, S = iso[0], iso[1]
+    return (p,) + _wide_tube(p, 400.0, vel=S.vel)
 
 
 def test_receiver_side_hankel_convergence(iso_wide):
@@ -160,7 +162,7 @@ def test_receiver_side_vti_far_field(vti):
     """VTI: the receiver-side sum of the closed-form labels (tube widened to 400 m) against the
     stationary-phase evaluation of the exact plane-wave integral, and against the source-side sum."""
     p0 = vti[0]
-    p, S, lab, X, Z, edge = (p0,) + _wide_tube(p0, 400.0)
+    p, S, lab, X, Z, edge = (p0,) + _wide_tube(p0, 400.0, vel=vti[1].vel)
     m = p.meta
     om = 2 * math.pi * 60.0
     v_of = lambda th: CF.thomsen_vti_phase_velocity(th, m['vp0'], m['vs0'], m['eps'], m['delta'])
