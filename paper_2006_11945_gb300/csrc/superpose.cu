@@ -177,15 +177,16 @@ __device__ __forceinline__ float lift_branch(float alpha, float a) {
 // spreading of the beam family never vanishes and the labels change continuously in pseudo-time,
 // so sampled often enough this follows its argument from the straight-ray initial data to the
 // steady state, which carries it onto the argument continued along the ray.
-// One thread per (x, z) column and chunk of TRACK_CHUNK angle planes marches through them with the
+// One thread per (x, z) column and chunk of `chunk` angle planes marches through them with the
 // column's b and vartheta of planes k-1, k, k+1 in registers, so a value is read from memory about
-// once; the x and z neighbours come through L1/L2 (neighbouring blocks advance nearly in step).
-constexpr int TRACK_CHUNK = 32;
+// chunk / (chunk + 2) times per cell; the x and z neighbours come through L1/L2 (neighbouring
+// blocks advance nearly in step).  The chunk shrinks on small grids so that the launch still fills
+// the GPU (launch_track_branch).
 __global__ void k_track_branch(Grid2D g, const float *__restrict__ st, const float *__restrict__ vel,
-                               float iw0, float *__restrict__ alpha, int init) {
+                               float iw0, float *__restrict__ alpha, int init, int chunk) {
     int ix = blockIdx.x * blockDim.x + threadIdx.x;
     int iz = blockIdx.y;
-    int k0 = blockIdx.z * TRACK_CHUNK, k1 = min(k0 + TRACK_CHUNK, g.nth);
+    int k0 = blockIdx.z * chunk, k1 = min(k0 + chunk, g.nth);
     if (ix >= g.nx) return;
     float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
     const float *B = st, *Th = st + 2 * g.field;
@@ -216,8 +217,13 @@ __global__ void k_track_branch(Grid2D g, const float *__restrict__ st, const flo
 
 cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cudaStream_t s) {
     const Grid2D &g = sv.g;
-    dim3 grid((g.nx + 127) / 128, g.nz, (g.nth + TRACK_CHUNK - 1) / TRACK_CHUNK);
-    k_track_branch<<<grid, 128, 0, s>>>(g, st, sv.vel, (float)(1.0 / sv.w0), sv.alpha, init ? 1 : 0);
+    // planes per thread: 32, halved while the launch would have fewer than 2^18 threads (about one
+    // full wave of 152 SMs x 2048), down to 2; rows of up to 128 threads, multiples of 32
+    const int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
+    int chunk = 32;
+    while (chunk > 2 && (int64_t)g.nx * g.nz * ((g.nth + chunk - 1) / chunk) < (1 << 18)) chunk /= 2;
+    dim3 grid((g.nx + bx - 1) / bx, g.nz, (g.nth + chunk - 1) / chunk);
+    k_track_branch<<<grid, bx, 0, s>>>(g, st, sv.vel, (float)(1.0 / sv.w0), sv.alpha, init ? 1 : 0, chunk);
     return cudaGetLastError();
 }
 
