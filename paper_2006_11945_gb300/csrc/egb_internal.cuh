@@ -231,6 +231,7 @@ cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, void *
                          cudaStream_t cap);
 // One sample of the continued spreading argument from the padded FP32 state st (init: first sample).
 cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cudaStream_t s);
+cudaError_t launch_track_batch(Solve *const *sv, const float *const *st, int n, bool init, cudaStream_t s);
 cudaError_t launch_superpose(Solve &sv, float2 *u_dev, uint8_t *count_dev, double *T_dev,
                              float *A_dev, int kmax, unsigned *d_err, cudaStream_t s);
 size_t superpose_scratch_bytes(const Solve &sv);

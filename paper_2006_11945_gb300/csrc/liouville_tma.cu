@@ -734,9 +734,15 @@ cudaError_t evolve_batch(Solve **sv, int n, int steps, StageDesc *d_desc, void *
             }
         }
         j += seg;
-        for (int i = 0; i < n && e == cudaSuccess; ++i)
-            if ((sv[i]->steps + j) % BRANCH_SAMPLE == 0)
-                e = launch_track_branch(*sv[i], sv[i]->state[(sv[i]->cur + j) % 3], false, s);
+        // one launch samples every due solve (per TRACK_BATCH solves)
+        std::vector<Solve *> due;
+        std::vector<const float *> due_st;
+        for (int i = 0; i < n; ++i)
+            if ((sv[i]->steps + j) % BRANCH_SAMPLE == 0) {
+                due.push_back(sv[i]);
+                due_st.push_back(sv[i]->state[(sv[i]->cur + j) % 3]);
+            }
+        if (e == cudaSuccess && !due.empty()) e = launch_track_batch(due.data(), due_st.data(), (int)due.size(), false, s);
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);

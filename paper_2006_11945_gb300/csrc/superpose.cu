@@ -181,13 +181,38 @@ __device__ __forceinline__ float lift_branch(float alpha, float a) {
 // column's b and vartheta of planes k-1, k, k+1 in registers, so a value is read from memory about
 // chunk / (chunk + 2) times per cell; the x and z neighbours come through L1/L2 (neighbouring
 // blocks advance nearly in step).  The chunk shrinks on small grids so that the launch still fills
-// the GPU (launch_track_branch).
-__global__ void k_track_branch(Grid2D g, const float *__restrict__ st, const float *__restrict__ vel,
-                               float iw0, float *__restrict__ alpha, int init, int chunk) {
-    int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    int iz = blockIdx.y;
-    int k0 = blockIdx.z * chunk, k1 = min(k0 + chunk, g.nth);
-    if (ix >= g.nx) return;
+// the GPU.  One launch serves up to TRACK_BATCH solves (a batch samples all its due solves at once):
+// their descriptors travel in the kernel's parameter block and its blocks are numbered across them.
+constexpr int TRACK_BATCH = 16;
+constexpr int TRACK_THREADS = 128;
+struct TrackDesc {
+    Grid2D g;
+    const float *st;   // padded state being sampled
+    const float *vel;  // [6][cells]
+    float *alpha;      // [cells]
+    float iw0;
+    int chunk, bx, nbx, nkc;  // planes per thread, row width, blocks along x, chunks along theta
+    int block_begin;          // first block of this solve in the launch
+};
+struct TrackBatch {
+    TrackDesc d[TRACK_BATCH];
+    int n, init;
+};
+
+__global__ void __launch_bounds__(TRACK_THREADS) k_track_branch(const __grid_constant__ TrackBatch TB) {
+    int i = 0;
+    while (i + 1 < TB.n && (int)blockIdx.x >= TB.d[i + 1].block_begin) ++i;
+    const TrackDesc &T = TB.d[i];
+    const Grid2D &g = T.g;
+    const int lb = (int)blockIdx.x - T.block_begin;
+    const int bxi = lb % T.nbx, rest = lb / T.nbx;
+    const int iz = rest % g.nz, kc = rest / g.nz;
+    const int ix = bxi * T.bx + (int)threadIdx.x;
+    if ((int)threadIdx.x >= T.bx || ix >= g.nx) return;
+    const int k0 = kc * T.chunk, k1 = min(k0 + T.chunk, g.nth);
+    const float *__restrict__ st = T.st;
+    const float *__restrict__ vel = T.vel;
+    float *__restrict__ alpha = T.alpha;
     float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
     const float *B = st, *Th = st + 2 * g.field;
     const int64_t p0 = pidx(g, 0, iz, ix), cells = (int64_t)g.nth * g.nx * g.nz;
@@ -207,24 +232,51 @@ __global__ void k_track_branch(Grid2D g, const float *__restrict__ st, const flo
         float tt = wrap_angle(tn - tm) * 0.5f * idth;
         int64_t o = o0 + (int64_t)k * oplane;
         float a = 0.f;
-        bool ok = cell_ref_arg(bx, bz, bt, tx, tz, tt, vel[o], vel[cells + o], vel[2 * cells + o], iw0, a);
-        if (init) alpha[o] = ok ? a : 0.f;
+        bool ok = cell_ref_arg(bx, bz, bt, tx, tz, tt, vel[o], vel[cells + o], vel[2 * cells + o], T.iw0, a);
+        if (TB.init) alpha[o] = ok ? a : 0.f;
         else if (ok) alpha[o] = lift_branch(alpha[o], a);
         bm = bc; tm = tc;
         bc = bn; tc = tn;
     }
 }
 
+cudaError_t launch_track_batch(Solve *const *sv, const float *const *st, int n, bool init, cudaStream_t s) {
+    for (int i0 = 0; i0 < n; i0 += TRACK_BATCH) {
+        TrackBatch TB;
+        TB.n = n - i0 < TRACK_BATCH ? n - i0 : TRACK_BATCH;
+        TB.init = init ? 1 : 0;
+        int64_t blocks = 0;
+        for (int j = 0; j < TB.n; ++j) {
+            const Solve &v = *sv[i0 + j];
+            const Grid2D &g = v.g;
+            TrackDesc &T = TB.d[j];
+            T.g = g;
+            T.st = st[i0 + j];
+            T.vel = v.vel;
+            T.alpha = v.alpha;
+            T.iw0 = (float)(1.0 / v.w0);
+            // planes per thread: 32, halved while the solve would have fewer than 2^18 threads
+            // (about one full wave of 152 SMs x 2048), down to 2; rows of up to 128 threads
+            T.bx = g.nx >= TRACK_THREADS ? TRACK_THREADS : ((g.nx + 31) / 32) * 32;
+            T.chunk = 32;
+            while (T.chunk > 2 && (int64_t)g.nx * g.nz * ((g.nth + T.chunk - 1) / T.chunk) < (1 << 18)) T.chunk /= 2;
+            T.nbx = (g.nx + T.bx - 1) / T.bx;
+            T.nkc = (g.nth + T.chunk - 1) / T.chunk;
+            T.block_begin = (int)blocks;
+            blocks += (int64_t)T.nbx * g.nz * T.nkc;
+        }
+        if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+        if (blocks > 0) k_track_branch<<<(unsigned)blocks, TRACK_THREADS, 0, s>>>(TB);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_track_branch(const Solve &sv, const float *st, bool init, cudaStream_t s) {
-    const Grid2D &g = sv.g;
-    // planes per thread: 32, halved while the launch would have fewer than 2^18 threads (about one
-    // full wave of 152 SMs x 2048), down to 2; rows of up to 128 threads, multiples of 32
-    const int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
-    int chunk = 32;
-    while (chunk > 2 && (int64_t)g.nx * g.nz * ((g.nth + chunk - 1) / chunk) < (1 << 18)) chunk /= 2;
-    dim3 grid((g.nx + bx - 1) / bx, g.nz, (g.nth + chunk - 1) / chunk);
-    k_track_branch<<<grid, bx, 0, s>>>(g, st, sv.vel, (float)(1.0 / sv.w0), sv.alpha, init ? 1 : 0, chunk);
-    return cudaGetLastError();
+    Solve *one[1] = {const_cast<Solve *>(&sv)};
+    const float *sts[1] = {st};
+    return launch_track_batch(one, sts, 1, init, s);
 }
 
 struct cf { float re, im; };
