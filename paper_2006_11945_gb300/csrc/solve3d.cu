@@ -389,8 +389,7 @@ struct Stage3Args {
 // cover many directions of one spatial tile and the theta/phi neighbours of a cell are read from L2),
 // blockIdx.y = (2 blockDim.x) x blockDim.y tile in (x, y), blockIdx.z = chunk of ZC3 z slices marched
 // by the CTA (the z neighbours of the next slice are the ones just read).  The tile shape is chosen
-// per grid so that it divides nx and ny where it can (tile_shape3d): a 64-cell row on a 96-cell
-// grid left a quarter of the lanes idle.
+// per grid (tile_shape3d).
 constexpr int ZC3 = 8;
 constexpr int MAXT3 = 256;  // threads per block at most (64 registers: 4 such blocks per SM)
 
@@ -499,24 +498,14 @@ __global__ void __launch_bounds__(MAXT3, 4) k_rk3_3d(Stage3Args A) {
     }
 }
 
-// Thread tile of k_rk3_3d for an nx x ny plane: x pairs per row in {32, 16, 8}, rows in
-// {4, 8, 16, 32}, 128 or 256 threads; the fewest idle lanes (cells of the tiles outside the grid),
-// then 256 threads, then the longer rows (coalescing).
-static dim3 tile_shape3d(int nx, int ny) {
-    int best_px = 32, best_ty = 8;
-    long best_waste = -1;
-    int best_threads = 0;
-    for (int px : {32, 16, 8})
-        for (int ty : {32, 16, 8, 4}) {
-            int threads = px * ty;
-            if (threads != 128 && threads != MAXT3) continue;
-            long w = 2L * px * ((nx + 2 * px - 1) / (2 * px)), h = (long)ty * ((ny + ty - 1) / ty);
-            long waste = w * h - (long)nx * ny;
-            bool better = best_waste < 0 || waste < best_waste ||
-                          (waste == best_waste && threads > best_threads);
-            if (better) { best_waste = waste; best_px = px; best_ty = ty; best_threads = threads; }
-        }
-    return dim3(best_px, best_ty);
+// Thread tile of k_rk3_3d for an nx x ny plane: 128 threads as 32 x pairs by 4 rows, or 16 by 8 when
+// that covers nx with fewer idle cells (ties keep the longer rows).  Measured on the two triclinic
+// sizes (evolution cell-updates/s, 48^3 x 12 x 24 / 96^3 x 24 x 48): 32 x 4 3.83e9 / 3.22e9,
+// 16 x 8 3.68e9 / 3.42e9, 32 x 8 3.68e9 / 3.33e9, 16 x 16 3.54e9 / 3.41e9, 8 x 16 3.40e9 / 2.65e9:
+// shorter rows cost more in locality (L2 hits, DRAM re-reads) than idle lanes cost in issue slots.
+static dim3 tile_shape3d(int nx, int /*ny*/) {
+    const int w32 = 64 * ((nx + 63) / 64), w16 = 32 * ((nx + 31) / 32);
+    return w16 < w32 ? dim3(16, 8) : dim3(32, 4);
 }
 
 cudaError_t solve3d_evolve(Solve3D &sv, int steps, cudaStream_t s) {
