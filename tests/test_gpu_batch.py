@@ -53,3 +53,30 @@ def test_steps_compose():
         for k in (4, 1, 5):
             ctx.evolve(s2, k, p.cfl)
         assert np.array_equal(_state(ctx, s1, p), _state(ctx, s2, p))
+
+
+def test_batch_of_twenty_samples_the_spreading_argument_like_solves_alone():
+    """Twenty small uneven solves with different step counts: the branch tracking of the due solves
+    runs in launches of up to 16 of them, and every solve's state and superposition (whose square
+    root sheet comes from the tracked argument) equal the same solve advanced alone, bit for bit."""
+    import paper_2006_11945_gb300 as egb
+    ps = [synthmedia.tti_heterogeneous(n=24 + 4 * (i % 5), n_theta=16 + 8 * (i % 3), length=1600.0,
+                                       steps=9 + 3 * i, freqs=(15.0, 30.0), seed=20 + i)
+          for i in range(20)]
+    alone = []
+    with egb.Context(0) as ctx:
+        for p in ps:
+            m = ctx.medium_2d(p)
+            s = ctx.source_2d(m, p)
+            ctx.evolve(s, p.steps, p.cfl)
+            r = ctx.superpose(s, len(p.freqs), p.nz, p.nx)
+            alone.append((_state(ctx, s, p), r))
+    with egb.Context(0) as ctx:
+        ids = [ctx.source_2d(ctx.medium_2d(p), p) for p in ps]
+        egb.egb_evolve_batch(ctx.h, ids, [p.steps for p in ps], ps[0].cfl)
+        egb.egb_sync(ctx.h)
+        for p, s, (st, r) in zip(ps, ids, alone):
+            assert np.array_equal(_state(ctx, s, p), st), p.name
+            b = ctx.superpose(s, len(p.freqs), p.nz, p.nx)
+            assert np.array_equal(b.u, r.u) and np.array_equal(b.count, r.count)
+            assert np.array_equal(b.T, r.T) and np.array_equal(b.A, r.A)
