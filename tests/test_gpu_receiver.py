@@ -38,11 +38,15 @@ def _oracle(p):
     return OS.green_receiver(S, lab, p.omegas, p.beam_width)
 
 
-@pytest.mark.parametrize('case', ['vti', 'tti'])
+@pytest.mark.parametrize('case', ['vti', 'vti_ragged', 'tti'])
 def test_receiver_side_matches_the_oracle(case):
     if case == 'vti':
         p = dataclasses.replace(synthmedia.vti_homogeneous(n=64, n_theta=64, steps=150, freqs=(30.0, 60.0)),
                                 R_sigma=200.0)
+    elif case == 'vti_ragged':
+        # rows of 45 receivers (a block serves 32) and 44 angles (8 warps take 6 or 5 of them)
+        p = dataclasses.replace(synthmedia.vti_homogeneous(n=45, n_theta=44, steps=100, freqs=(30.0,)),
+                                R_sigma=150.0)
     else:
         p = synthmedia.tti_heterogeneous(n=64, n_theta=96, length=2560.0, steps=400, freqs=(20.0, 40.0, 80.0),
                                          beam_width=150.0)
