@@ -38,11 +38,16 @@ def _oracle(p):
     return OS.green_receiver(S, lab, p.omegas, p.beam_width)
 
 
-@pytest.mark.parametrize('case', ['vti', 'vti_ragged', 'tti'])
+@pytest.mark.parametrize('case', ['vti', 'vti_ragged', 'vti_10_freqs', 'tti'])
 def test_receiver_side_matches_the_oracle(case):
     if case == 'vti':
         p = dataclasses.replace(synthmedia.vti_homogeneous(n=64, n_theta=64, steps=150, freqs=(30.0, 60.0)),
                                 R_sigma=200.0)
+    elif case == 'vti_10_freqs':
+        # more frequencies than one pass of the kernel accumulates (8)
+        p = dataclasses.replace(synthmedia.vti_homogeneous(n=40, n_theta=32, steps=80,
+                                                           freqs=tuple(10.0 + 5.0 * i for i in range(10))),
+                                R_sigma=150.0)
     elif case == 'vti_ragged':
         # rows of 45 receivers (a block serves 32) and 44 angles (8 warps take 6 or 5 of them)
         p = dataclasses.replace(synthmedia.vti_homogeneous(n=45, n_theta=44, steps=100, freqs=(30.0,)),
