@@ -626,7 +626,6 @@ __global__ void k_arrivals(SupArgs A, uint8_t *count, double *T, float *Aout, in
     int64_t cells = (int64_t)g.nth * g.nx * g.nz;
     float idth = (float)(1.0 / g.dth);
     const float pi8 = 25.1327412287183459f;
-    float Tl[KMAX_LIMIT];
     double Td[KMAX_LIMIT];
     float Al[KMAX_LIMIT];
     int n = 0, total = 0;
@@ -663,7 +662,6 @@ __global__ void k_arrivals(SupArgs A, uint8_t *count, double *T, float *Aout, in
             if (n < kmax) ++n;
         }
     }
-    (void)Tl;
     if (total > kmax) atomicOr(A.err, DeviceErrors::OVERFLOW);
     int64_t node = (int64_t)iz * g.nx + ix;
     if (count) count[node] = (uint8_t)n;
