@@ -908,6 +908,38 @@ def serve_requests(duration, seed=4, rate=200.0, large_scale=1.0):
     return out
 
 
+def measure_serve_curve(rates=(5.0, 10.0, 20.0, 40.0, 80.0, 160.0), seconds=4.0, large_scale=0.25,
+                        chunk=60, chunk_work=4e9, max_chunk_work=2e10):
+    """Offered against sustained load: the serving loop on Poisson streams of increasing rate (the
+    same 50/50 mix, large requests scaled by large_scale), arrivals admitted for `seconds`, then
+    everything admitted drained.  Per rate: offered requests/s, completed and never-admitted
+    requests, completed/s over the whole run, p50/p99 latency of the completed ones."""
+    from paper_2006_11945_gb300.serve import Backend, serve
+    points = []
+    be = Backend(0)
+    # warm-up: the first solve of each grid shape runs the stencil autotuner, the first of each
+    # medium its characteristic velocities
+    serve(serve_requests(2.0, seed=9, rate=8.0, large_scale=large_scale), be, chunk_steps=chunk,
+          chunk_work=chunk_work, max_chunk_work=max_chunk_work)
+    for rate in rates:
+        reqs = serve_requests(seconds, rate=rate, large_scale=large_scale)
+        st = serve(reqs, be, chunk_steps=chunk, time_limit=seconds, chunk_work=chunk_work,
+                   max_chunk_work=max_chunk_work)
+        s = st.summary(len(reqs))
+        points.append({'offered_per_s': len(reqs) / seconds, 'offered': len(reqs), 'completed': s['completed'],
+                       'not_admitted': s['not_admitted'], 'completed_per_s': s['solves_per_s'],
+                       'p50_s': s['p50_latency_s'], 'p99_s': s['p99_latency_s'], 'wall_s': s['wall_s'],
+                       'device_cell_updates_per_s': s['device_cell_updates_per_s']})
+    be.close()
+    n = int(512 * large_scale) // 4 * 4
+    return {'metric': 'serving: completed solves/s against offered requests/s', 'unit': 'solves/s',
+            'config': {'workload': f'Poisson streams, {seconds:g} s of arrivals each, 50/50 64x64x64 VTI / '
+                                   f'{n}^2 x {max(16, int(256 * large_scale))} TTI, 1-8 frequencies, '
+                                   'admitted ones drained', 'chunk_steps': chunk, 'chunk_work': chunk_work,
+                       'max_chunk_work': max_chunk_work},
+            'points': points}
+
+
 def run_serve(args):
     """Serving measurement: arrivals for --serve-seconds, then drain what was admitted."""
     import torch
@@ -959,7 +991,7 @@ def main():
     ap.add_argument('--impl', default='egb', choices=['egb', 'reference'])
     ap.add_argument('--workload', default='tti512',
                     choices=['tti512', 'tti256', 'tti128', 'vti64', 'tri96', 'tri48', 'batch', 'serve',
-                             'zmarch'])
+                             'serve_curve', 'zmarch'])
     ap.add_argument('--zm-theta', type=int, default=256)
     ap.add_argument('--zm-n', type=int, default=512)
     ap.add_argument('--zm-drt', type=int, default=0, choices=[0, 1])
@@ -984,6 +1016,10 @@ def main():
     args = ap.parse_args()
     if args.impl == 'reference':
         run_reference(args)
+    elif args.workload == 'serve_curve':
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_serve_curve()))
     elif args.workload == 'serve':
         run_serve(args)
     elif args.reductions:
