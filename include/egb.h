@@ -157,8 +157,10 @@ egb_status egb_superpose(egb_ctx *ctx, egb_solve_id solve, void *u_out, uint8_t 
  * a Gaussian beam is launched back along the ray through (x0, theta): the level-set Jacobian at x0
  * is the ray propagator to the ray's closest approach C to x_s (Sec. 4, the dynamic ray tracing of
  * Eqs. 21-24 read from the labels), which gives the beam's width and curvature there (Eq. 25), its
- * amplitude (Eq. 26) and its phase at x_s, tau + M b^2 / 2 (b the ray's offset from x_s at C).
- * The sum over theta at x0, weighted as the source side (calibrated to (i/4) H0^(1) in a
+ * amplitude (Eq. 26) and its phase at x_s, tau + M b^2 / 2 (b the ray's offset from x_s at C);
+ * Im M comes from the beam's Wronskian, which the ray propagator keeps, so every term decays away
+ * from its ray even where the discrete label Jacobian is poorly conditioned.  The sum over theta
+ * at x0, weighted as the source side (calibrated to (i/4) H0^(1) in a
  * homogeneous isotropic medium), is rescaled by rho_s c_s^2 / (rho0 c0^2) to egb_superpose's
  * normalisation.  Valid for arrivals without a caustic (KMAH index 0; principal square root); the
  * beams reach x_s about as wide as w(r) = w0 sqrt(1 + (2 r / (k w0^2))^2), so the source-ray tube
