@@ -64,9 +64,17 @@ __device__ __forceinline__ void eigvec_for(const Sym3T<R> &G, R lam, R g[3]) {
     g[2] = best[2] * inv;
 }
 
-// Largest eigenvalue and unit eigenvector of a symmetric 3x3 matrix (qP branch).
+// Relative gap (lambda_1 - lambda_2) / lambda_1 between the two largest eigenvalues below which the
+// FP32 path recomputes a cell in FP64 from the input moduli: near a qP-qS degeneracy the eigenvector
+// is sensitive to rounding as (rounding) / gap, and at a gap of 1e-5 FP32 moduli and arithmetic
+// cost about 5e-5 in the group velocity (1.5e-7 at gaps of 2e-3 and more).
+constexpr float QP_GAP_FP64 = 1e-3f;
+
+// Largest eigenvalue and unit eigenvector of a symmetric 3x3 matrix (qP branch); with rel_gap, also
+// the relative gap to the second eigenvalue from the same trigonometric roots (0 when all three
+// coincide).
 template <typename R>
-__device__ __forceinline__ R qp_eigen(const Sym3T<R> &G, R g[3]) {
+__device__ __forceinline__ R qp_eigen(const Sym3T<R> &G, R g[3], R *rel_gap = nullptr) {
     R m = (G.xx + G.yy + G.zz) * (R(1) / R(3));
     R b00 = G.xx - m, b11 = G.yy - m, b22 = G.zz - m;
     R p2 = (b00 * b00 + b11 * b11 + b22 * b22 +
@@ -74,6 +82,7 @@ __device__ __forceinline__ R qp_eigen(const Sym3T<R> &G, R g[3]) {
     R lam;
     if (p2 <= R(0)) {
         lam = m;
+        if (rel_gap) *rel_gap = R(0);
     } else {
         R p = sqrt(p2);
         R det = b00 * (b11 * b22 - G.yz * G.yz) - G.xy * (G.xy * b22 - G.yz * G.xz) +
@@ -82,6 +91,12 @@ __device__ __forceinline__ R qp_eigen(const Sym3T<R> &G, R g[3]) {
         r = r > R(1) ? R(1) : (r < R(-1) ? R(-1) : r);
         R phi = acos(r) * (R(1) / R(3));
         lam = m + R(2) * p * cos(phi);
+        if (rel_gap) {
+            // the smallest root at phi + 2 pi / 3; the middle one from the trace
+            R l3 = m + R(2) * p * cos(phi + R(2.0943951023931954923));
+            R l2 = R(3) * m - lam - l3;
+            *rel_gap = (lam - l2) / lam;
+        }
     }
     eigvec_for(G, lam, g);
     lam = quad(G, g);
@@ -106,10 +121,11 @@ using RayVel = RayVelT<float>;
 
 // Full per-cell solve: phase velocity, group velocity, dp/dt, dtheta/dt.
 template <typename R>
-__device__ __forceinline__ RayVelT<R> ray_velocity2d(const R *a, const R *dax, const R *daz, R s, R c) {
+__device__ __forceinline__ RayVelT<R> ray_velocity2d(const R *a, const R *dax, const R *daz, R s, R c,
+                                                     R *rel_gap = nullptr) {
     Sym3T<R> G = christoffel2d(a, s, c);
     R g[3];
-    R lam = qp_eigen(G, g);
+    R lam = qp_eigen(G, g, rel_gap);
     RayVelT<R> r;
     r.v = sqrt(lam);
     R iv = R(1) / r.v;
@@ -127,10 +143,10 @@ using SrcVel = SrcVelT<float>;
 
 // Source-medium quantities at phase angle theta (no gradients).
 template <typename R>
-__device__ __forceinline__ SrcVelT<R> source_velocity(const R *a, R s, R c) {
+__device__ __forceinline__ SrcVelT<R> source_velocity(const R *a, R s, R c, R *rel_gap = nullptr) {
     Sym3T<R> G = christoffel2d(a, s, c);
     R g[3];
-    R lam = qp_eigen(G, g);
+    R lam = qp_eigen(G, g, rel_gap);
     SrcVelT<R> r;
     r.v = sqrt(lam);
     R iv = R(1) / r.v;
@@ -186,10 +202,10 @@ template <typename R> struct RayVel3T { R v, V[3], pd[3]; };
 // dp_i/dt = -1/2 g . Gamma(d_i a, p) . g with p = n / v.
 template <typename R>
 __device__ __forceinline__ RayVel3T<R> ray_velocity3d(const R *a, const R *dax, const R *day, const R *daz,
-                                                      const R n[3]) {
+                                                      const R n[3], R *rel_gap = nullptr) {
     Sym3T<R> G = christoffel3d(a, n);
     R g[3];
-    R lam = qp_eigen(G, g);
+    R lam = qp_eigen(G, g, rel_gap);
     RayVel3T<R> r;
     r.v = sqrt(lam);
     R iv = R(1) / r.v, iv2 = iv * iv;

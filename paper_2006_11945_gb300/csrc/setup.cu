@@ -120,17 +120,33 @@ __global__ void k_source(Medium m, double xs, double zs, int nth, float *src) {
     float as[21];
 #pragma unroll
     for (int q = 0; q < 21; ++q) as[q] = interp(m.a + (int64_t)q * nodes);
+    // near a qP-qS degeneracy (relative gap below QP_GAP_FP64): the source medium in FP64, the
+    // moduli a = c / rho of the four nodes from the inputs, interpolated in double
+    auto polished = [&](double sd, double cd) {
+        double ad[21];
+        for (int q = 0; q < 21; ++q) {
+            auto A = [&](int n) { return (double)m.c21[(int64_t)n * 21 + q] / (double)m.rho[n]; };
+            ad[q] = (1 - tz) * ((1 - tx) * A(n00) + tx * A(n00 + 1)) +
+                    tz * ((1 - tx) * A(n00 + m.nx) + tx * A(n00 + m.nx + 1));
+        }
+        SrcVelT<double> r = source_velocity<double>(ad, sd, cd);
+        return SrcVel{(float)r.v, (float)r.Vx, (float)r.Vz, (float)r.Vn};
+    };
     if (k == 0) {
         for (int q = 0; q < 21; ++q) src[q] = as[q];
         src[21] = interp(m.rho);
-        SrcVel r0 = source_velocity(as, 0.f, 1.f);
+        float gap0 = 1.f;
+        SrcVel r0 = source_velocity(as, 0.f, 1.f, &gap0);
+        if (!(gap0 >= QP_GAP_FP64)) r0 = polished(0.0, 1.0);
         src[22] = r0.v;
         src[23] = 0.f;
     }
     if (k >= nth) return;
     double th = 2.0 * M_PI * k / nth;
     float s = (float)sin(th), c = (float)cos(th);
-    SrcVel r = source_velocity(as, s, c);
+    float gap = 1.f;
+    SrcVel r = source_velocity(as, s, c, &gap);
+    if (!(gap >= QP_GAP_FP64)) r = polished(sin(th), cos(th));
     src[src_ps(k)] = s / r.v;
     src[src_ps(k) + 1] = c / r.v;
     src[src_sc(nth, k)] = s;
@@ -138,6 +154,22 @@ __global__ void k_source(Medium m, double xs, double zs, int nth, float *src) {
 }
 
 // ------------------------------- velocities ------------------------------------------------------
+// One phase cell's ray velocities in FP64 from the input stiffness and density (a = c / rho exactly
+// as the FP64 inputs give it), for cells whose qP eigenvalue lies within QP_GAP_FP64 of the next.
+__device__ RayVel polished_velocity2d(const Medium &m, int node, const float *dx, const float *dz, int k, int nth) {
+    double ad[21], dxd[21], dzd[21];
+    const double rho = (double)m.rho[node];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) {
+        ad[q] = (double)m.c21[(int64_t)node * 21 + q] / rho;
+        dxd[q] = (double)dx[q];
+        dzd[q] = (double)dz[q];
+    }
+    const double th = 2.0 * M_PI * k / nth;
+    RayVelT<double> r = ray_velocity2d<double>(ad, dxd, dzd, sin(th), cos(th));
+    return RayVel{(float)r.v, (float)r.Vx, (float)r.Vz, (float)r.pdx, (float)r.pdz, (float)r.td};
+}
+
 __global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, float *__restrict__ vel,
                            float *__restrict__ velp, float *rate_out) {
     int node = blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,7 +187,9 @@ __global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, fl
         float ihx = (float)(1.0 / g.hx), ihz = (float)(1.0 / g.hz), idth = (float)(1.0 / g.dth);
         for (int k = 0; k < g.nth; ++k) {
             float s = src[src_sc(g.nth, k)], c = src[src_sc(g.nth, k) + 1];
-            RayVel r = ray_velocity2d(a, dx, dz, s, c);
+            float gap = 1.f;
+            RayVel r = ray_velocity2d(a, dx, dz, s, c, &gap);
+            if (!(gap >= QP_GAP_FP64)) r = polished_velocity2d(m, node, dx, dz, k, g.nth);
             int64_t o = (int64_t)k * nodes + node;
             vel[o] = r.Vx;
             vel[cells + o] = r.Vz;

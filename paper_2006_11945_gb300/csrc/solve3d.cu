@@ -241,6 +241,7 @@ __global__ void k_source3d(Grid3D g, const float *__restrict__ c21, const float 
 // ------------------------------- velocities ----------------------------------------------------
 __global__ void k_velocity3d(Grid3D g, const float *__restrict__ a, const float *__restrict__ dax,
                              const float *__restrict__ day, const float *__restrict__ daz,
+                             const float *__restrict__ c21, const float *__restrict__ rho,
                              float *__restrict__ vel, float *rate_out) {
     extern __shared__ float tab[];  // sin th, cos th [nth], sin ph, cos ph [nph]
     float *sth = tab, *cth = tab + g.nth, *sph = tab + 2 * g.nth, *cph = tab + 2 * g.nth + g.nph;
@@ -272,10 +273,33 @@ __global__ void k_velocity3d(Grid3D g, const float *__restrict__ a, const float 
         for (int k = 0; k < g.nph; ++k)
             for (int j = 0; j < g.nth; ++j) {
                 float n[3] = {sth[j] * cph[k], sth[j] * sph[k], cth[j]};
-                RayVel3T<float> r = ray_velocity3d(A, DX, DY, DZ, n);
+                float gap = 1.f;
+                RayVel3T<float> r = ray_velocity3d(A, DX, DY, DZ, n, &gap);
                 float nth_[3] = {cth[j] * cph[k], cth[j] * sph[k], -sth[j]};
                 float td = r.v * (nth_[0] * r.pd[0] + nth_[1] * r.pd[1] + nth_[2] * r.pd[2]);
                 float pd = r.v * (-sph[k] * r.pd[0] + cph[k] * r.pd[1]) / sth[j];
+                if (!(gap >= QP_GAP_FP64)) {
+                    // near a qP-qS degeneracy: the cell in FP64 from the input stiffness and density
+                    double ad[21], dxd[21], dyd[21], dzd[21];
+                    for (int q = 0; q < 21; ++q) {
+                        ad[q] = a_node(c21, rho, node, q);
+                        dxd[q] = DX[q];
+                        dyd[q] = DY[q];
+                        dzd[q] = DZ[q];
+                    }
+                    const double th = (j + 0.5) * M_PI / g.nth, ph = 2.0 * M_PI * k / g.nph;
+                    const double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
+                    const double nd[3] = {st * cp, st * sp, ct};
+                    RayVel3T<double> rd = ray_velocity3d<double>(ad, dxd, dyd, dzd, nd);
+                    const double ntd[3] = {ct * cp, ct * sp, -st};
+                    td = (float)(rd.v * (ntd[0] * rd.pd[0] + ntd[1] * rd.pd[1] + ntd[2] * rd.pd[2]));
+                    pd = (float)(rd.v * (-sp * rd.pd[0] + cp * rd.pd[1]) / st);
+                    r.v = (float)rd.v;
+                    for (int i = 0; i < 3; ++i) {
+                        r.V[i] = (float)rd.V[i];
+                        r.pd[i] = (float)rd.pd[i];
+                    }
+                }
                 int64_t o = (int64_t)(k * g.nth + j) * g.nodes + node;
                 float out[9] = {r.V[0], r.V[1], r.V[2], td, pd, r.v, r.pd[0], r.pd[1], r.pd[2]};
 #pragma unroll
@@ -363,7 +387,8 @@ cudaError_t solve3d_setup(Solve3D &sv, float *d_rate, cudaStream_t s) {
     const Medium &m = *sv.m;
     k_source3d<<<(ndir + 127) / 128, 128, 0, s>>>(g, m.c21, m.rho, sv.xs[0], sv.xs[1], sv.xs[2], sv.gs64, sv.src);
     size_t tab = (size_t)(2 * g.nth + 2 * g.nph) * sizeof(float);
-    k_velocity3d<<<(unsigned)((g.nodes + 127) / 128), 128, tab, s>>>(g, m.a, m.dadx, m.dady, m.dadz, sv.vel, d_rate);
+    k_velocity3d<<<(unsigned)((g.nodes + 127) / 128), 128, tab, s>>>(g, m.a, m.dadx, m.dady, m.dadz, m.c21, m.rho,
+                                                                     sv.vel, d_rate);
     dim3 gf((g.nx + 127) / 128, g.ny * g.nz, ndir);
     k_frozen3d<<<gf, 128, 0, s>>>(g, sv.gs64, sv.xs[0], sv.xs[1], sv.xs[2], sv.r0, sv.R_sigma, sv.frozen);
     dim3 gi((g.pitch + 127) / 128, (g.nz + 4) * g.rows, ndir);

@@ -286,6 +286,26 @@ def tti_heterogeneous(n=512, h=5.0, n_theta=256, steps=None, freqs=(10.0, 20.0, 
                                            centres=centres.tolist(), length=L))
 
 
+def triclinic_near_degenerate(n=32, h=10.0, n_theta=64, steps=40, freqs=(15.0,), beam_width=50.0, cfl=0.5):
+    """Homogeneous triclinic medium whose qP eigenvalue nearly meets the next one in the x-z plane.
+
+    Voigt matrix C = B B^T + 0.05 I with B a 6 x 6 standard normal draw of PCG64 seed 39760, scaled
+    to C33 = rho (3000 m/s)^2, rho = 2200 kg/m^3, then rotated about y by -0.0338158 rad.  The seed
+    and the rotation come from a search over seeded draws with an FP64 eigen-solve (not part of
+    this generator): in this medium the relative gap between the two largest eigenvalues of the
+    Christoffel matrix is 6.8e-5 at the phase angles theta = 0 and pi of the x-z plane.
+    """
+    B = np.random.Generator(np.random.PCG64(39760)).standard_normal((6, 6))
+    C = B @ B.T + 0.05 * np.eye(6)
+    rho = 2200.0
+    C = C * (rho * 3000.0 ** 2 / C[2, 2])
+    C = rotate_voigt_about_y(np.broadcast_to(C, (n, n, 6, 6)), np.full((n, n), -0.0338158))
+    c21, r = _pack(C, np.full((n, n), rho))
+    xs = ((n // 2) * h, (n // 2) * h)
+    return Problem2D('triclinic_near_degenerate', n, n, h, h, c21, r, xs, n_theta, list(freqs), beam_width,
+                     steps, cfl, meta=dict(seed=39760, tilt=-0.0338158))
+
+
 def tti_default_steps(n, h):
     """Pseudo-time steps for the TTI medium: 1.1 x (latest exit time of source rays) / dt.
 

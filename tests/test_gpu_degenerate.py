@@ -1,0 +1,33 @@
+"""Characteristic velocities near a qP-qS degeneracy (the FP64 polish of the FP32 eigen-solve).
+
+In synthmedia.triclinic_near_degenerate the relative gap between the two largest Christoffel
+eigenvalues is 6.8e-5 at theta = 0 and pi.  There the qP eigenvector turns quickly with the
+direction: the FP32 closed form on FP32 moduli gives group velocities off by about 7e-4 (an
+emulation of it in numpy float32).  Cells whose gap is below QP_GAP_FP64 are recomputed in FP64
+from the input stiffness and density, so the stored velocities and the source block's reference
+velocity equal the FP64 oracle's to FP32 rounding in every cell.
+"""
+import numpy as np
+import pytest
+
+import synthmedia
+
+pytestmark = pytest.mark.gpu
+
+
+def test_velocities_near_a_qp_qs_degeneracy_match_the_oracle():
+    import paper_2006_11945_gb300 as egb
+    from oracle import liouville as OL
+    p = synthmedia.triclinic_near_degenerate()
+    with egb.Context(0) as ctx:
+        m = ctx.medium_2d(p)
+        s = ctx.source_2d(m, p)
+        vel = ctx.read_velocity(s, p.n_theta, p.nz, p.nx).astype(np.float64)
+        info = egb.egb_get_solve_info(ctx.h, s)
+    S = OL.Setup(p)
+    speed = np.hypot(S.vel['Vx'], S.vel['Vz'])
+    err = np.hypot(vel[0] - S.vel['Vx'], vel[1] - S.vel['Vz']) / speed
+    err_v = np.abs(vel[3] - S.vel['v']) / S.vel['v']
+    print('group velocity rel error: max', err.max(), 'at theta = 0', err[0].max(), '; phase velocity', err_v.max())
+    assert err.max() < 2e-6 and err_v.max() < 1e-6
+    assert abs(info['c_ref'] - S.c_ref) / S.c_ref < 1e-6

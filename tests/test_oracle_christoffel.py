@@ -123,3 +123,19 @@ def test_positive_definite_check():
     bad = good.copy()
     bad[synthmedia.voigt21_index(3, 3)] = -1.0
     assert MD.is_positive_definite(np.stack([good, bad])).tolist() == [True, False]
+
+
+def test_near_degenerate_medium_has_the_stated_gap():
+    """The input of the GPU test on the FP64 polish: positive definite, and the two largest
+    Christoffel eigenvalues come within 6.8e-5 (relative) at theta = 0 and pi, not elsewhere."""
+    import synthmedia
+    from oracle import medium as MD
+    p = synthmedia.triclinic_near_degenerate()
+    assert MD.is_positive_definite(p.c21[:1].astype(np.float64)).all()
+    a = MD.density_normalised(p.c21[0].astype(np.float64), float(p.rho[0]))
+    th = 2 * np.pi * np.arange(p.n_theta) / p.n_theta
+    n = np.stack([np.sin(th), np.zeros_like(th), np.cos(th)], -1)
+    w = np.linalg.eigvalsh(CH.christoffel(a, n))
+    gap = (w[:, -1] - w[:, -2]) / w[:, -1]
+    assert abs(gap[0] - 6.8e-5) < 1e-6 and abs(gap[p.n_theta // 2] - 6.8e-5) < 1e-6
+    assert np.sort(gap)[2] > 1e-3
