@@ -538,11 +538,11 @@ __global__ void __launch_bounds__(RX_W * RX_WARPS) k_sum_receiver(SupArgs A, con
     const float c0 = source_velocity(a0, 0.f, 1.f).v;  // qP phase velocity along +z at x0
     const float rho0 = A.rho[node], rho_s = A.src[21], c_s = A.src[22];
     const float four_pi = 12.5663706143591729f;
-    for (int w0 = 0; w0 < A.n_omega; w0 += RX_MAXW) {
-        const int nw = min(RX_MAXW, A.n_omega - w0);
+    for (int wb = 0; wb < A.n_omega; wb += RX_MAXW) {  // first frequency of this pass
+        const int nw = min(RX_MAXW, A.n_omega - wb);
         __syncthreads();  // as[] loaded; the previous pass's partial sums consumed
         if (threadIdx.x < nw) {  // omega as a double-float pair (hi, lo)
-            double om = A.omega_dev[w0 + threadIdx.x];
+            double om = A.omega_dev[wb + threadIdx.x];
             float hi = (float)om;
             ohs[threadIdx.x] = hi;
             ols[threadIdx.x] = (float)(om - (double)hi);
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(RX_W * RX_WARPS) k_sum_receiver(SupArgs A, con
                 sre += part[q][w][lane].x;
                 sim += part[q][w][lane].y;
             }
-            if (rx) u[((int64_t)(w0 + w) * g.nz + iz) * g.nx + ix] = make_float2(sc * sre, sc * sim);
+            if (rx) u[((int64_t)(wb + w) * g.nz + iz) * g.nx + ix] = make_float2(sc * sre, sc * sim);
         }
     }
 }
