@@ -183,7 +183,7 @@ egb_status egb_superpose_receiver(egb_ctx *ctx, egb_solve_id solve, void *u_out)
  * the process exits.  Restrictions:
  *   - u_out, count, T, A must be device pointers (or NULL); host pointers give EGB_E_INVALID;
  *   - a solve whose superposition needs more scratch than EGB_NOALLOC_SCRATCH_BYTES (about
- *     9 bytes per phase-space cell plus the beam-centre lists, i.e. up to a few million cells) is
+ *     5 bytes per phase-space cell plus the beam-centre lists, i.e. up to a few million cells) is
  *     refused with EGB_E_INVALID and a message giving both sizes;
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress with
  *     that device current); make that first call before any stream capture.  The array is taken

@@ -4,7 +4,7 @@
 // closest approach; a cell counts when its labels come from the source manifold (q > 1/2) and it
 // is not itself frozen.
 //
-//  k_beam_fields   per cell: b, source flag, |V_s(vartheta)|                          (Eq. 35)
+//  k_beam_fields   per cell: b and the source flag                                    (Eq. 35)
 //  k_centres       per grid line (row: fixed z, or column: fixed x) and angle: every sign change of
 //                  b between flagged neighbours is a beam centre; its level-set gradients give the
 //                  dynamic ray tracing (Eqs. 21-24) -> complex Hessian M (Eq. 25), spreading det C
@@ -28,7 +28,7 @@ struct SupArgs {
     const float *vel;   // [6][cells]
     const float *rho;   // [nz][nx]
     const float *src;   // source block
-    float *B, *VSN;     // [cells]
+    float *B;           // [cells]
     uint8_t *FL;        // [cells]
     // beam centres: rows [nth][nz][KC], columns [nth][nx][KC]
     int *rcnt, *ccnt;
@@ -51,20 +51,13 @@ __device__ __forceinline__ float wrap_angle(float d) {
 
 __global__ void k_beam_fields(SupArgs A) {
     const Grid2D &g = A.g;
-    __shared__ float as[21];
-    if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
-    __syncthreads();
     int ix = blockIdx.x * blockDim.x + threadIdx.x;
     int iz = blockIdx.y, k = blockIdx.z;
     if (ix >= g.nx) return;
     int64_t p = pidx(g, k, iz, ix);
-    float b = A.st[p], q = A.st[g.field + p], th = A.st[2 * g.field + p];
-    float s, c;
-    sincosf(th, &s, &c);
-    SrcVel r = source_velocity(as, s, c);
+    float b = A.st[p], q = A.st[g.field + p];
     int64_t o = cidx(g, k, iz, ix);
     A.B[o] = b;
-    A.VSN[o] = r.Vn;
     // rays that carry source labels and have left the frozen manifold
     A.FL[o] = (q > 0.5f && !A.frozen[o]) ? 1 : 0;
 }
@@ -618,6 +611,9 @@ constexpr int KMAX_LIMIT = 32;
 
 __global__ void k_arrivals(SupArgs A, uint8_t *count, double *T, float *Aout, int kmax) {
     const Grid2D &g = A.g;
+    __shared__ float as[21];
+    if (threadIdx.x < 21) as[threadIdx.x] = A.src[threadIdx.x];
+    __syncthreads();
     int ix = blockIdx.x * blockDim.x + threadIdx.x;
     int iz = blockIdx.y;
     if (ix >= g.nx) return;
@@ -630,10 +626,15 @@ __global__ void k_arrivals(SupArgs A, uint8_t *count, double *T, float *Aout, in
     float Al[KMAX_LIMIT];
     int n = 0, total = 0;
     auto B = [&](int k) { return A.B[cidx(g, (k + g.nth) % g.nth, iz, ix)]; };
+    // the geometrical amplitude of a crossing cell, with |V_s| of the source medium at its vartheta
+    // (only crossing cells need it)
     auto acell = [&](int k, float bt) {
         int64_t o = cidx(g, k, iz, ix);
         float vr = A.vel[3 * cells + o];
-        return c_ref * c_ref * sqrtf(rho_s / rho_r) / (vr * sqrtf(pi8 * A.VSN[o] * fabsf(bt)));
+        float sth, cth;
+        sincosf(A.st[2 * g.field + pidx(g, k, iz, ix)], &sth, &cth);
+        const float vsn = source_velocity(as, sth, cth).Vn;
+        return c_ref * c_ref * sqrtf(rho_s / rho_r) / (vr * sqrtf(pi8 * vsn * fabsf(bt)));
     };
     for (int k = 0; k < g.nth; ++k) {
         int kn = (k + 1) % g.nth;
@@ -676,7 +677,7 @@ size_t superpose_scratch_bytes(const Solve &sv) {
     size_t cells = (size_t)g.nth * g.nx * g.nz;
     size_t rs = (size_t)g.nth * g.nz * KC, cs = (size_t)g.nth * g.nx * KC;
     size_t no = sv.omega.size();
-    size_t b = cells * (4 + 4 + 1);
+    size_t b = cells * (4 + 1);  // B, FL
     b = (b + 255) & ~(size_t)255;
     b += (size_t)g.nth * (g.nz + g.nx) * 4 + 256;
     b += (rs + cs) * 8 + 512;
@@ -749,7 +750,6 @@ static cudaError_t superpose_args(Solve &sv, unsigned *d_err, cudaStream_t s, Su
     A.alpha = sv.alpha;
     A.iw0 = (float)(1.0 / sv.w0);
     A.B = (float *)take(cells * 4);
-    A.VSN = (float *)take(cells * 4);
     A.FL = (uint8_t *)take(cells);
     A.rcnt = (int *)take((size_t)g.nth * g.nz * 4);
     A.ccnt = (int *)take((size_t)g.nth * g.nx * 4);
