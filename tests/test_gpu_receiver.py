@@ -98,3 +98,20 @@ def test_receiver_side_argument_errors():
         with pytest.raises(egb.EgbError) as e:
             egb.egb_source(ctx.h, m, (p.xs[0], 0.0, p.xs[1]), p.omegas, 50.0, 16, r0=40.0, R_sigma=20.0)
         assert e.value.status == egb.EGB_E_INVALID
+
+
+def test_receiver_side_of_an_fp64_solve_matches_the_oracle():
+    """A solve of the plain FP64 form: egb_superpose_receiver converts its state before summing."""
+    import paper_2006_11945_gb300 as egb
+    p = dataclasses.replace(synthmedia.vti_homogeneous(n=48, n_theta=48, steps=100, freqs=(30.0, 45.0)),
+                            R_sigma=150.0)
+    with egb.Context(0, precision=egb.EGB_FP64) as ctx:
+        m = ctx.medium_2d(p)
+        s = ctx.source_2d(m, p)
+        ctx.evolve(s, p.steps, p.cfl)
+        ur = ctx.superpose_receiver(s, len(p.freqs), p.nz, p.nx).astype(np.complex128)
+        egb.egb_sync(ctx.h)
+    ref = _oracle(p)
+    rel = np.linalg.norm(ur - ref) / np.linalg.norm(ref)
+    print('FP64-form receiver-side parity', rel)
+    assert np.all(np.isfinite(ur)) and rel < 2e-3
