@@ -90,12 +90,14 @@ __device__ __forceinline__ R qp_eigen(const Sym3T<R> &G, R g[3], R *rel_gap = nu
         R r = det / (R(2) * p2 * p);
         r = r > R(1) ? R(1) : (r < R(-1) ? R(-1) : r);
         R phi = acos(r) * (R(1) / R(3));
-        lam = m + R(2) * p * cos(phi);
+        const R cphi = cos(phi);
+        lam = m + R(2) * p * cphi;
         if (rel_gap) {
-            // the smallest root at phi + 2 pi / 3; the middle one from the trace
-            R l3 = m + R(2) * p * cos(phi + R(2.0943951023931954923));
-            R l2 = R(3) * m - lam - l3;
-            *rel_gap = (lam - l2) / lam;
+            // lambda_1 - lambda_2 = 2 sqrt(3) p sin(pi/3 - phi) = 3 p cos phi - sqrt(3) p sin phi,
+            // with phi in [0, pi/3] so that sin phi = sqrt(1 - cos^2 phi)
+            const R s2 = R(1) - cphi * cphi;
+            const R sphi = sqrt(s2 > R(0) ? s2 : R(0));
+            *rel_gap = (R(3) * cphi - R(1.7320508075688772935) * sphi) * p / lam;
         }
     }
     eigvec_for(G, lam, g);

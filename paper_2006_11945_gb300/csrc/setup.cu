@@ -170,7 +170,10 @@ __device__ RayVel polished_velocity2d(const Medium &m, int node, const float *dx
     return RayVel{(float)r.v, (float)r.Vx, (float)r.Vz, (float)r.pdx, (float)r.pdz, (float)r.td};
 }
 
-__global__ void k_velocity(Medium m, Grid2D g, const float *__restrict__ src, float *__restrict__ vel,
+// At most 128 registers (the FP32 loop needs about 100; the rarely taken FP64 polish would otherwise
+// double the allocation and halve the resident warps of every launch).
+__global__ void __launch_bounds__(128, 4) k_velocity(Medium m, Grid2D g, const float *__restrict__ src,
+                                                     float *__restrict__ vel,
                            float *__restrict__ velp, float *rate_out) {
     int node = blockIdx.x * blockDim.x + threadIdx.x;
     int nodes = g.nx * g.nz;

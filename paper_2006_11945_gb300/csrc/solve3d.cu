@@ -239,7 +239,9 @@ __global__ void k_source3d(Grid3D g, const float *__restrict__ c21, const float 
 }
 
 // ------------------------------- velocities ----------------------------------------------------
-__global__ void k_velocity3d(Grid3D g, const float *__restrict__ a, const float *__restrict__ dax,
+// At most 170 registers (three 128-thread blocks per SM, as the FP32 loop alone needs; the rarely
+// taken FP64 polish would otherwise raise the allocation for every launch).
+__global__ void __launch_bounds__(128, 3) k_velocity3d(Grid3D g, const float *__restrict__ a, const float *__restrict__ dax,
                              const float *__restrict__ day, const float *__restrict__ daz,
                              const float *__restrict__ c21, const float *__restrict__ rho,
                              float *__restrict__ vel, float *rate_out) {
