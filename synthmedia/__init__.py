@@ -436,6 +436,22 @@ def vti_homogeneous_3d(n=32, h=10.0, n_theta=12, n_phi=24, steps=None, vp0=3000.
                      meta=dict(vp0=vp0, vs0=vs0, eps=eps, delta=delta, rho=rho))
 
 
+def triclinic_near_degenerate_3d(n=8, h=10.0, n_theta=12, n_phi=24, steps=4, freqs=(15.0,), beam_width=50.0,
+                                  cfl=0.5):
+    """The stiffness of triclinic_near_degenerate in a homogeneous cube, rotated about y by a further
+    pi / (2 n_theta), so that its near qP-qS degeneracy (relative gap 6.8e-5) lies along the grid
+    direction theta = pi / (2 n_theta) (the first polar cell centre), phi = 0."""
+    B = np.random.Generator(np.random.PCG64(39760)).standard_normal((6, 6))
+    C = B @ B.T + 0.05 * np.eye(6)
+    rho = 2200.0
+    C = C * (rho * 3000.0 ** 2 / C[2, 2])
+    C = rotate_voigt_about_y(C[None], np.array([-0.0338158 + np.pi / (2 * n_theta)]))[0]
+    c21, r = _cube(C, rho, n)
+    xs = ((n // 2) * h,) * 3
+    return Problem3D('triclinic_near_degenerate_3d', n, n, n, h, h, h, c21, r, xs, n_theta, n_phi,
+                     list(freqs), beam_width, steps, cfl, meta=dict(seed=39760))
+
+
 def triclinic_3d(n=96, h=10.0, n_theta=24, n_phi=48, steps=None, freqs=(15.0,), beam_width=50.0,
                  seed=5, cfl=0.5, length=None, vp=3000.0, vs=1700.0, rho=2300.0, amplitude=0.10,
                  sigma=150.0):

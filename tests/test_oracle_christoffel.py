@@ -139,3 +139,20 @@ def test_near_degenerate_medium_has_the_stated_gap():
     gap = (w[:, -1] - w[:, -2]) / w[:, -1]
     assert abs(gap[0] - 6.8e-5) < 1e-6 and abs(gap[p.n_theta // 2] - 6.8e-5) < 1e-6
     assert np.sort(gap)[2] > 1e-3
+
+
+def test_near_degenerate_cube_has_the_gap_on_a_grid_direction():
+    """The 3-D version: the gap of 6.8e-5 lies on the direction (first polar cell centre, phi = 0)
+    of the 3-D angle grid and its antipode, every other grid direction at least 1e-2."""
+    import synthmedia
+    from oracle import medium as MD
+    p = synthmedia.triclinic_near_degenerate_3d()
+    a = MD.density_normalised(p.c21[0].astype(np.float64), float(p.rho[0]))
+    th, ph = CH.angle_grid_3d(p.n_theta, p.n_phi)
+    gaps = {}
+    for k in range(p.n_phi):
+        for j in range(p.n_theta):
+            w = np.linalg.eigvalsh(CH.christoffel(a, CH.direction_3d(th[j], ph[k])))
+            gaps[(j, k)] = (w[-1] - w[-2]) / w[-1]
+    assert abs(gaps[(0, 0)] - 6.8e-5) < 1e-6 and abs(gaps[(p.n_theta - 1, p.n_phi // 2)] - 6.8e-5) < 1e-6
+    assert sorted(gaps.values())[2] > 1e-2
